@@ -1,0 +1,156 @@
+/*
+ * pluqmodp.h — C ABI of the GB300 (sm_103a) rank-profile-revealing PLUQ
+ * library over a prime field GF(p).
+ *
+ * Method: Dumas, Gautier, Pernet, Sultan, "Parallel computation of echelon
+ * forms" (arXiv:1402.3501).  The factorization is the tile-recursive
+ * elimination of Sec. 4.1 ("Tiled recursive elimination": recursive splitting
+ * into four quadrants, the bottom-left and top-right eliminations independent
+ * once the top-left one is done), built on the routines of Sec. 2.1: fgemm
+ * C <- alpha A B + beta C mod p with delayed modular reduction (Sec. 3.1),
+ * ftrsm, flaswp and fgetrf, which computes (P, L, U, Q) with L and U stored
+ * in place of A such that A = P L U Q.  The pivoting reveals both the row and
+ * the column rank profile (Sec. 4.1).
+ *
+ * Conventions shared by every entry point
+ *   - p is prime, 2 <= p < 2^31.  Matrix entries are uint32 residues in
+ *     [0, p), row-major with a leading dimension (elements, >= columns).
+ *   - Device pointers unless stated otherwise; the caller owns every buffer.
+ *   - Permutations are int32 index vectors: (P^T A)[t,:] = A[P[t],:] and
+ *     (A Q^T)[:,u] = A[:,Q[u]].  The first r entries of P and Q are the
+ *     pivots: {(P[k], Q[k]) : k < r} is the rank profile matrix of A.
+ *   - Compressed storage of B = P^T A Q^T: B[i,j] for i > j, j < r holds L
+ *     (unit diagonal implicit); B[i,j] for i <= j, i < r holds U (non-zero
+ *     diagonal); the trailing (m-r) x (n-r) block is zero.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *     enqueue work on it; the recursion reads block ranks back to the host,
+ *     so calls return once the factorization has been issued and its ranks
+ *     are known.  A context is not thread-safe; use one per host thread.
+ *   - m = 0 or n = 0 is valid: rank 0, identity permutations.
+ *   - Every call returns PLUQ_OK (0) or a negative status below.
+ */
+#ifndef PLUQMODP_H
+#define PLUQMODP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PLUQ_OK 0
+#define PLUQ_ERR_INVALID_ARG -1        /* negative size, ld < columns, NULL */
+#define PLUQ_ERR_P_NOT_PRIME -2        /* p fails a deterministic primality test */
+#define PLUQ_ERR_P_OUT_OF_RANGE -3     /* p < 2 or p >= 2^31 */
+#define PLUQ_ERR_ENTRY_OUT_OF_RANGE -4 /* an input entry is >= p */
+#define PLUQ_ERR_UNSUPPORTED_FORM -5   /* fgemm form unavailable for this p */
+#define PLUQ_ERR_NO_WORKSPACE -6       /* device workspace allocation failed */
+#define PLUQ_ERR_CUDA -7               /* a CUDA runtime call failed */
+#define PLUQ_ERR_TIMEOUT -8            /* a bounded device wait ran out */
+
+/* fgemm forms for the Schur-complement updates (Sec. 3.1).
+ *   FP64:     residues embedded in doubles, products on FP64 DMMA tensor
+ *             instructions, one reduction per k(p-1)^2 < 2^53 block (the
+ *             paper's floating-point embedding).
+ *   LIMB_F16: residues balanced and split into small signed limbs held
+ *             exactly in FP16, products on tcgen05 tensor cores with FP32
+ *             accumulation kept below 2^24, recombined and reduced once per
+ *             block; exact, like FP64.
+ *   AUTO:     LIMB_F16 where available for p, else FP64. */
+#define PLUQ_FORM_AUTO 0
+#define PLUQ_FORM_FP64 1
+#define PLUQ_FORM_LIMB_F16 2
+
+typedef struct pluq_ctx pluq_ctx;
+
+/* Create a context bound to CUDA device `device`; *ctx receives it.
+ * The context owns the device workspace (grown on demand, freed by
+ * pluq_destroy).  Errors: INVALID_ARG (ctx NULL), CUDA. */
+int pluq_create(pluq_ctx** ctx, int device);
+
+/* Release a context and its workspace.  NULL is accepted. */
+int pluq_destroy(pluq_ctx* ctx);
+
+/* Rank-profile-revealing PLUQ (getrf of Sec. 2.1, tile-recursive as in
+ * Sec. 4.1) of the m x n matrix A over GF(p), in place.
+ *   A        device, m x n, leading dimension lda >= n; on return holds the
+ *            compressed L\U of B = P^T A Q^T (see conventions).
+ *   P, Q     device int32, length m and n; receive the permutations.
+ *   rank_dev device int64 scalar (may be NULL); receives r.
+ *   rrp, crp device int32, length >= min(m,n) (either may be NULL); receive
+ *            the sorted row and column rank profiles in their first r entries.
+ *   form     PLUQ_FORM_*.
+ * Errors: INVALID_ARG, P_NOT_PRIME, P_OUT_OF_RANGE, ENTRY_OUT_OF_RANGE (A is
+ * left unmodified), UNSUPPORTED_FORM, NO_WORKSPACE, CUDA. */
+int pluq_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, uint32_t* A, int64_t lda,
+              int32_t* P, int32_t* Q, int64_t* rank_dev, int32_t* rrp, int32_t* crp,
+              int form, void* stream);
+
+/* Reduced row echelon form of A over GF(p) (the echelon form of Sec. 4.1,
+ * made canonical: pivots equal to 1, zeros above them, rows ordered by pivot
+ * column).  Computed from the PLUQ as R = (U Q)[:, CRP]^{-1} (U Q).
+ *   A        device, m x n, lda >= n; not modified (a workspace copy is
+ *            factored).
+ *   R        device, min(m,n) x n, ldr >= n; receives the r x n RREF in its
+ *            first r rows (rows r.. are left untouched).
+ *   rank_dev device int64 scalar (may be NULL).
+ *   crp      device int32, length >= min(m,n) (may be NULL): pivot columns.
+ * Errors: as pluq_modp. */
+int echelon_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_t* A,
+                 int64_t lda, uint32_t* R, int64_t ldr, int64_t* rank_dev, int32_t* crp,
+                 int form, void* stream);
+
+/* Rank and both rank profiles of A over GF(p) (Sec. 4.1), A unmodified.
+ *   rank_dev       device int64 scalar (may be NULL).
+ *   rrp, crp       device int32, length >= min(m,n) (may be NULL).
+ *   rpm_col_of_row device int32, length m (may be NULL): the rank profile
+ *                  matrix as a map row -> pivot column, -1 for rows outside
+ *                  the row rank profile.
+ * Errors: as pluq_modp. */
+int rank_profile_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_t* A,
+                      int64_t lda, int64_t* rank_dev, int32_t* rrp, int32_t* crp,
+                      int32_t* rpm_col_of_row, int form, void* stream);
+
+/* Schur-complement update C <- C - A B mod p (fgemm of Sec. 2.1 with
+ * alpha = -1, beta = 1, delayed reduction of Sec. 3.1), exposed for callers
+ * and kernel-level checks.
+ *   A  device, M x K, lda >= K;  B device, K x N, ldb >= N;
+ *   C  device, M x N, ldc >= N, updated in place.  C may not overlap A or B.
+ * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM, NO_WORKSPACE, CUDA. */
+int fgemm_modp(pluq_ctx* ctx, uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+               int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc, int form,
+               void* stream);
+
+/* Batched PLUQ of `batch` independent matrices (each as pluq_modp).
+ *   m, n, lda   host int64 arrays of length batch.
+ *   A, P, Q     host arrays of `batch` device pointers.
+ *   ranks       host int64 array of length batch; receives the ranks.
+ *   status      host int32 array of length batch (may be NULL): per-matrix
+ *               status codes.
+ * Returns the first failing status, else PLUQ_OK. */
+int pluq_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const int64_t* m,
+                      const int64_t* n, uint32_t* const* A, const int64_t* lda,
+                      int32_t* const* P, int32_t* const* Q, int64_t* ranks, int32_t* status,
+                      int form, void* stream);
+
+/* Host copy of the rank found by the last factorization on this context. */
+int pluq_last_rank(pluq_ctx* ctx, int64_t* rank);
+
+/* Tuning knobs of the recursion (base-case tile bm x bn, 1..128 each, and the
+ * diagonal block of the triangular solves, 1..64).  0 keeps the current
+ * value. */
+int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
+
+/* Counters of the last call: base-case launches, internal recursion nodes,
+ * fgemm calls. */
+int pluq_last_stats(pluq_ctx* ctx, int64_t* n_base, int64_t* n_nodes, int64_t* n_gemm);
+
+/* Human-readable name of a status code (static string). */
+const char* pluq_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLUQMODP_H */

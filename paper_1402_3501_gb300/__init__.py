@@ -1,0 +1,17 @@
+"""GB300-native rank-profile-revealing PLUQ / echelon forms over GF(p).
+
+Tile-recursive elimination (Dumas, Gautier, Pernet, Sultan, "Parallel
+computation of echelon forms", arXiv:1402.3501, Sec. 4.1) with hand-written
+CUDA kernels for sm_103a behind a C ABI (include/pluqmodp.h).  This package
+holds the CUDA sources (csrc/), the in-tree build (build.py) and the Python
+binding (binding.py).
+"""
+from .binding import (FORM_AUTO, FORM_FP64, FORM_LIMB_F16, Context, PluqError, PLUQResult,
+                      default_context, echelon_modp, fgemm_modp, load, pluq_modp,
+                      pluq_modp_batched, rank_profile_modp)
+
+__all__ = [
+    "FORM_AUTO", "FORM_FP64", "FORM_LIMB_F16", "Context", "PluqError", "PLUQResult",
+    "default_context", "echelon_modp", "fgemm_modp", "load", "pluq_modp", "pluq_modp_batched",
+    "rank_profile_modp",
+]

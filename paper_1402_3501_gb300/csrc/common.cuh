@@ -1,0 +1,107 @@
+// Shared declarations of the GF(p) PLUQ library: status codes, the context,
+// and the internal entry points each translation unit provides.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/pluqmodp.h"
+#include "field.cuh"
+
+#define PLUQ_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return PLUQ_ERR_CUDA;          \
+  } while (0)
+
+#define PLUQ_TRY(call)               \
+  do {                               \
+    int s_ = (call);                 \
+    if (s_ != PLUQ_OK) return s_;    \
+  } while (0)
+
+static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// A growable device allocation owned by the context.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need) {
+    if (need <= bytes) return PLUQ_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    size_t want = need + need / 8 + 256;
+    if (cudaMalloc(&ptr, want) != cudaSuccess) {
+      cudaGetLastError();
+      return PLUQ_ERR_NO_WORKSPACE;
+    }
+    bytes = want;
+    return PLUQ_OK;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(ptr); }
+};
+
+// Upper bound on the recursion depth of the tile-recursive driver (each level
+// halves at least one dimension, and dimensions are < 2^31).
+constexpr int kMaxDepth = 72;
+
+struct pluq_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  FieldP F{};
+  int form = PLUQ_FORM_FP64;
+  int bm = 128, bn = 128;  // base-case tile
+  int trsm_block = 64;     // diagonal block of the triangular solves
+  int64_t mmax = 0, nmax = 0;
+  // workspace
+  DevBuf scratch;          // uint32 gathers, packed GEMM operands
+  DevBuf pack;             // packed limb / fp64 GEMM operands
+  DevBuf perm_r, perm_c;   // int32 [kMaxDepth][mmax], [kMaxDepth][nmax]
+  DevBuf tmp_i;            // int32 scratch for segment permutations
+  DevBuf small;            // int32 / int64 scalars (rank, flags)
+  DevBuf inv_table;        // uint32[p] inverses when p is small
+  uint32_t inv_table_p = 0;
+  DevBuf work;             // a copy of A for echelon / rank-profile calls
+  int32_t* host_small = nullptr;  // pinned host scalars
+  // per-call statistics (host side)
+  int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
+  // device error flag (int) lives in small at offset 0
+};
+
+// kernels / helpers implemented in the .cu files
+int launch_base_pluq(pluq_ctx* c, uint32_t* A, int64_t lda, int m, int n, int32_t* perm_r,
+                     int32_t* perm_c, int32_t* rank_out);
+int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
+int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t count);
+int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const int64_t* seg_len,
+                   int nseg);
+int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
+                 const int32_t* perm);
+int permute_cols(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
+                 const int32_t* perm);
+int trsm_left_lower_unit(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r, uint32_t* B,
+                         int64_t ldb, int64_t ncols);
+int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
+                     int64_t ldb, int64_t nrows);
+int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
+                    int64_t ldb, int64_t ncols);
+// C <- C - A B (mod p); A M x K, B K x N, C M x N, all row-major uint32.
+int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
+              const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
+int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+                   int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
+int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+                   int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
+int limb_form_supported(uint32_t p);
+int fp64_form_supported(uint32_t p);
+int ensure_inv_table(pluq_ctx* c);
+const uint32_t* inv_table_ptr(pluq_ctx* c);

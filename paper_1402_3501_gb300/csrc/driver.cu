@@ -1,0 +1,569 @@
+// Host driver of the tile-recursive PLUQ (Sec. 4.1, "Tiled recursive
+// elimination"), the C ABI, and the output kernels (rank profiles, rank
+// profile matrix, reduced echelon form).
+//
+// Recursion, for a block A = [A1 A2; A3 A4] (A1 of size m1 x n1), in place:
+//   A1 = P1 [L1; M1] [U1 V1] Q1                      (recursive, rank r1)
+//   [B1; B2] = P1^T A2,  [C1 C2] = A3 Q1^T           (row / column gathers)
+//   D = L1^{-1} B1,  E = C1 U1^{-1}                   (ftrsm)
+//   F = B2 - M1 D,  H = A4 - E D,  G = C2 - E V1      (fgemm, F and H as one)
+//   F = P2 [L2; M2] [U2 V2] Q2,  G = P3 [L3; M3] [U3 V3] Q3   (recursive; independent)
+//   H <- P3^T H Q2^T = [H1 H2; H3 H4]
+//   [I; K] = [H1; H3] U2^{-1}                         (ftrsm)
+//   [H2; H4] -= [I; K] V2                             (fgemm)
+//   O = L3^{-1} H2,  R = H4 - M3 O                    (ftrsm, fgemm)
+//   R = P4 [L4; M4] [U4 V4] Q4                        (recursive, rank r4)
+// followed by the block-cyclic shifts that bring the four pivot blocks to the
+// front: rows [A1p F2p | F_rest | G3p R4p] -> [A1p F2p G3p R4p | F_rest ...],
+// columns [A1p | G3p G_rest | F2p R4p] -> [A1p F2p G3p R4p | G_rest ...].
+// The L entries of the G-pivot rows on the F-pivot columns are I (not
+// L3^{-1} I): G-pivot row = I [0 U2 V2] + L3 [U3 0 O] on the column blocks.
+// Each recursive call returns local index vectors for its rows and columns;
+// the caller applies them to the parts of its block outside the child and
+// composes them into its own.  The pivots of the four calls together are the
+// rank profile matrix because every call keeps its non-pivot rows and
+// columns in their original relative order.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace {
+
+bool is_prime_u32(uint32_t n) {
+  if (n < 2) return false;
+  for (uint32_t d : {2u, 3u, 5u, 7u, 11u, 13u}) {
+    if (n % d == 0) return n == d;
+  }
+  // deterministic Miller-Rabin for n < 3,215,031,751 with bases 2, 3, 5, 7
+  uint64_t d = n - 1;
+  int s = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    ++s;
+  }
+  for (uint64_t a : {2ull, 3ull, 5ull, 7ull}) {
+    uint64_t x = 1, b = a % n, e = d;
+    while (e) {
+      if (e & 1) x = x * b % n;
+      b = b * b % n;
+      e >>= 1;
+    }
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < s; ++i) {
+      x = x * x % n;
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+int check_p(uint32_t p) {
+  if (p < 2 || p >= 0x80000000u) return PLUQ_ERR_P_OUT_OF_RANGE;
+  if (!is_prime_u32(p)) return PLUQ_ERR_P_NOT_PRIME;
+  return PLUQ_OK;
+}
+
+int resolve_form(uint32_t p, int form) {
+  if (form == PLUQ_FORM_AUTO) {
+    if (limb_form_supported(p)) return PLUQ_FORM_LIMB_F16;
+    if (fp64_form_supported(p)) return PLUQ_FORM_FP64;
+    return -1;
+  }
+  if (form == PLUQ_FORM_FP64) return fp64_form_supported(p) ? form : -1;
+  if (form == PLUQ_FORM_LIMB_F16) return limb_form_supported(p) ? form : -1;
+  return -2;
+}
+
+__global__ void k_check_range(const uint32_t* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                              uint32_t p, int* __restrict__ flag) {
+  for (int64_t t = blockIdx.y; t < m; t += gridDim.y) {
+    const uint32_t* row = A + t * lda;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x)
+      if (row[u] >= p) *flag = 1;
+  }
+}
+
+__global__ void k_copy_mat(uint32_t* __restrict__ dst, int64_t ldd, const uint32_t* __restrict__ src,
+                           int64_t lds, int64_t m, int64_t n) {
+  for (int64_t t = blockIdx.y; t < m; t += gridDim.y) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x)
+      dst[t * ldd + u] = src[t * lds + u];
+  }
+}
+
+// Sorted set of the first r entries of a permutation of [0, cnt): a bitmap in
+// shared memory, then an ordered compaction (one CTA).
+__global__ void k_profile(const int32_t* __restrict__ perm, int64_t r, int64_t cnt,
+                          int32_t* __restrict__ out) {
+  extern __shared__ uint32_t bits[];
+  __shared__ int32_t warp_tot[32];
+  const int64_t words = (cnt + 31) / 32;
+  for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+  __syncthreads();
+  for (int64_t k = threadIdx.x; k < r; k += blockDim.x) {
+    const int32_t v = perm[k];
+    atomicOr(&bits[v >> 5], 1u << (v & 31));
+  }
+  __syncthreads();
+  // each thread owns a contiguous range of words
+  const int64_t per = (words + blockDim.x - 1) / blockDim.x;
+  const int64_t w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+  int32_t mine = 0;
+  for (int64_t w = w0; w < w1; ++w) mine += __popc(bits[w]);
+  // block exclusive scan of `mine`
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x / 32;
+    int32_t v = lane < nw ? warp_tot[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) warp_tot[lane] = v;  // inclusive warp totals
+  }
+  __syncthreads();
+  int32_t pos = incl - mine + (warp > 0 ? warp_tot[warp - 1] : 0);
+  for (int64_t w = w0; w < w1; ++w) {
+    uint32_t b = bits[w];
+    while (b) {
+      const int bit = __ffs(b) - 1;
+      out[pos++] = (int32_t)(w * 32 + bit);
+      b &= b - 1;
+    }
+  }
+}
+
+__global__ void k_rpm_col_of_row(const int32_t* __restrict__ P, const int32_t* __restrict__ Q,
+                                 int64_t r, int64_t m, int32_t* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) out[t] = -1;
+}
+__global__ void k_rpm_fill(const int32_t* __restrict__ P, const int32_t* __restrict__ Q, int64_t r,
+                           int32_t* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < r) out[P[k]] = Q[k];
+}
+
+__global__ void k_invert_perm(const int32_t* __restrict__ Q, int64_t n, int32_t* __restrict__ qinv) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) qinv[Q[u]] = (int32_t)u;
+}
+
+// RREF row t = pivot ord[t] (ord[t] = qinv[crp[t]]) of X = [I | U1^{-1} U2]
+// in the Q frame, scattered back to the original column order.
+__global__ void k_rref_scatter(const uint32_t* __restrict__ W, int64_t ldw, int64_t r, int64_t n,
+                               const int32_t* __restrict__ qinv, const int32_t* __restrict__ crp,
+                               uint32_t* __restrict__ R, int64_t ldr) {
+  for (int64_t t = blockIdx.y; t < r; t += gridDim.y) {
+    const int32_t k = qinv[crp[t]];
+    for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < n;
+         col += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t j = qinv[col];
+      R[t * ldr + col] = j < r ? (j == k ? 1u : 0u) : W[(int64_t)k * ldw + j];
+    }
+  }
+}
+
+__global__ void k_store_rank(int64_t* dst, int64_t r) { *dst = r; }
+
+dim3 grid2(int64_t rows, int64_t cols) {
+  int64_t gx = cdiv(cols, 256);
+  if (gx > 32) gx = 32;
+  int64_t gy = rows < 65535 ? rows : 65535;
+  if (gy < 1) gy = 1;
+  if (gx < 1) gx = 1;
+  return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
+struct Recursion {
+  pluq_ctx* c;
+  uint32_t* A;
+  int64_t lda;
+  int32_t* rank_slot;  // device int32
+  int32_t* PR(int d) { return c->perm_r.as<int32_t>() + (int64_t)d * c->mmax; }
+  int32_t* PC(int d) { return c->perm_c.as<int32_t>() + (int64_t)d * c->nmax; }
+  uint32_t* X(int64_t R0, int64_t C0, int64_t i, int64_t j) {
+    return A + (R0 + i) * lda + (C0 + j);
+  }
+
+  int64_t split(int64_t x) { return x / 2; }
+
+  int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out) {
+    int32_t* pr = PR(d) + R0;
+    int32_t* pc = PC(d) + C0;
+    *r_out = 0;
+    if (m == 0 || n == 0) {
+      PLUQ_TRY(launch_iota(c, pr, m));
+      PLUQ_TRY(launch_iota(c, pc, n));
+      return PLUQ_OK;
+    }
+    if (m <= c->bm && n <= c->bn) {
+      c->n_base++;
+      PLUQ_TRY(launch_base_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      PLUQ_CUDA(cudaMemcpyAsync(c->host_small, rank_slot, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                c->stream));
+      PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+      *r_out = c->host_small[0];
+      return PLUQ_OK;
+    }
+    if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
+    c->n_nodes++;
+    const int64_t m1 = m > c->bm ? split(m) : m;
+    const int64_t n1 = n > c->bn ? split(n) : n;
+    const int64_t m2 = m - m1, n2 = n - n1;
+    int32_t* cr = PR(d + 1);
+    int32_t* cc = PC(d + 1);
+    PLUQ_TRY(launch_iota(c, pr, m));
+    PLUQ_TRY(launch_iota(c, pc, n));
+
+    // A1
+    int64_t r1 = 0;
+    PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1));
+    PLUQ_TRY(launch_compose(c, pr, cr + R0, m1));
+    PLUQ_TRY(launch_compose(c, pc, cc + C0, n1));
+    PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
+    PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
+    if (r1 > 0) {
+      PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2));
+      PLUQ_TRY(trsm_right_upper(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2));
+      PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
+                         X(R0, C0, r1, n1), lda));
+      PLUQ_TRY(fgemm_sub(c, m2, n1 - r1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, r1), lda,
+                         X(R0, C0, m1, r1), lda));
+    }
+
+    // F (rows r1..m1 of the top half, right columns)
+    int64_t r2 = 0;
+    PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2));
+    PLUQ_TRY(launch_compose(c, pr + r1, cr + R0 + r1, m1 - r1));
+    PLUQ_TRY(launch_compose(c, pc + n1, cc + C0 + n1, n2));
+    PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
+    PLUQ_TRY(permute_cols(c, X(R0, C0, 0, n1), lda, r1, n2, cc + C0 + n1));       // D
+    PLUQ_TRY(permute_cols(c, X(R0, C0, m1, n1), lda, m2, n2, cc + C0 + n1));      // H
+
+    // G (bottom rows, columns r1..n1 of the left half)
+    int64_t r3 = 0;
+    PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3));
+    PLUQ_TRY(launch_compose(c, pr + m1, cr + R0 + m1, m2));
+    PLUQ_TRY(launch_compose(c, pc + r1, cc + C0 + r1, n1 - r1));
+    PLUQ_TRY(permute_rows(c, X(R0, C0, m1, 0), lda, m2, r1, cr + R0 + m1));   // E
+    PLUQ_TRY(permute_rows(c, X(R0, C0, m1, n1), lda, m2, n2, cr + R0 + m1));  // H
+    PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
+
+    // H = [H1 H2; H3 H4] at rows m1.., columns n1..
+    if (r2 > 0) {
+      PLUQ_TRY(trsm_right_upper(c, X(R0, C0, r1, n1), lda, r2, X(R0, C0, m1, n1), lda, m2));
+      PLUQ_TRY(fgemm_sub(c, m2, n2 - r2, r2, X(R0, C0, m1, n1), lda, X(R0, C0, r1, n1 + r2), lda,
+                         X(R0, C0, m1, n1 + r2), lda));
+    }
+    if (r3 > 0) {
+      PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, m1, r1), lda, r3, X(R0, C0, m1, n1 + r2), lda,
+                                    n2 - r2));
+      PLUQ_TRY(fgemm_sub(c, m2 - r3, n2 - r2, r3, X(R0, C0, m1 + r3, r1), lda,
+                         X(R0, C0, m1, n1 + r2), lda, X(R0, C0, m1 + r3, n1 + r2), lda));
+    }
+
+    // R
+    int64_t r4 = 0;
+    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4));
+    PLUQ_TRY(launch_compose(c, pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3));
+    PLUQ_TRY(launch_compose(c, pc + n1 + r2, cc + C0 + n1 + r2, n2 - r2));
+    PLUQ_TRY(permute_rows(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, r1 + r3,
+                          cr + R0 + m1 + r3));  // E2, M3
+    PLUQ_TRY(permute_rows(c, X(R0, C0, m1 + r3, n1), lda, m2 - r3, r2,
+                          cr + R0 + m1 + r3));  // K
+    PLUQ_TRY(permute_cols(c, X(R0, C0, 0, n1 + r2), lda, r1 + r2, n2 - r2,
+                          cc + C0 + n1 + r2));  // D2, V2
+    PLUQ_TRY(permute_cols(c, X(R0, C0, m1, n1 + r2), lda, r3, n2 - r2,
+                          cc + C0 + n1 + r2));  // O
+
+    // block-cyclic shifts
+    int32_t* tmp = PR(kMaxDepth - 1);  // spare row slot
+    {
+      const int64_t a = r1 + r2, fr = m1 - r1 - r2, gr = r3 + r4;
+      if (fr > 0 && gr > 0) {
+        const int64_t st[2] = {fr, 0}, ln[2] = {gr, fr};
+        PLUQ_TRY(launch_segperm(c, tmp, st, ln, 2));
+        PLUQ_TRY(permute_rows(c, X(R0, C0, a, 0), lda, fr + gr, n, tmp));
+        PLUQ_TRY(launch_compose(c, pr + a, tmp, fr + gr));
+      }
+    }
+    {
+      // columns from r1: [G3p (r3) | G_rest (n1-r1-r3) | F2p (r2) | R4p (r4)]
+      const int64_t gn = n1 - r1 - r3;
+      const bool ident = (r2 == 0 || (r3 == 0 && gn == 0)) && (r4 == 0 || gn == 0);
+      if (!ident) {
+        int32_t* tmpc = PC(kMaxDepth - 1);
+        const int64_t st[4] = {r3 + gn, 0, r3 + gn + r2, r3};
+        const int64_t ln[4] = {r2, r3, r4, gn};
+        const int64_t len = r3 + gn + r2 + r4;
+        PLUQ_TRY(launch_segperm(c, tmpc, st, ln, 4));
+        PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, m, len, tmpc));
+        PLUQ_TRY(launch_compose(c, pc + r1, tmpc, len));
+      }
+    }
+    *r_out = r1 + r2 + r3 + r4;
+    return PLUQ_OK;
+  }
+};
+
+int prepare(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, int form, void* stream) {
+  PLUQ_TRY(check_p(p));
+  const int f = resolve_form(p, form);
+  if (f == -2) return PLUQ_ERR_INVALID_ARG;
+  if (f < 0) return PLUQ_ERR_UNSUPPORTED_FORM;
+  PLUQ_CUDA(cudaSetDevice(c->device));
+  c->stream = (cudaStream_t)stream;
+  c->F = make_field(p);
+  c->form = f;
+  c->n_base = c->n_nodes = c->n_gemm = 0;
+  (void)m;
+  (void)n;
+  return PLUQ_OK;
+}
+
+// Factor A in place; leaves P = PR(0), Q = PC(0) in the workspace.
+int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t* r_out) {
+  c->mmax = std::max<int64_t>(m, 1);
+  c->nmax = std::max<int64_t>(n, 1);
+  PLUQ_TRY(c->perm_r.ensure(sizeof(int32_t) * kMaxDepth * c->mmax));
+  PLUQ_TRY(c->perm_c.ensure(sizeof(int32_t) * kMaxDepth * c->nmax));
+  PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * std::max<int64_t>(m * n, 1)));
+  PLUQ_TRY(c->tmp_i.ensure(sizeof(int32_t) * std::max(c->mmax, c->nmax)));
+  PLUQ_TRY(c->small.ensure(256));
+  PLUQ_TRY(ensure_inv_table(c));
+  int* flag = c->small.as<int>();
+  PLUQ_CUDA(cudaMemsetAsync(flag, 0, 256, c->stream));
+  if (m > 0 && n > 0) {
+    k_check_range<<<grid2(m, n), 256, 0, c->stream>>>(A, lda, m, n, c->F.p, flag);
+    PLUQ_CUDA(cudaGetLastError());
+    PLUQ_CUDA(cudaMemcpyAsync(c->host_small, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->host_small[0] != 0) return PLUQ_ERR_ENTRY_OUT_OF_RANGE;
+  }
+  Recursion rec{c, A, lda, c->small.as<int32_t>() + 8};
+  PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out));
+  c->host_small[8] = (int32_t)*r_out;
+  return PLUQ_OK;
+}
+
+int write_outputs(pluq_ctx* c, int64_t m, int64_t n, int64_t r, int32_t* P, int32_t* Q,
+                  int64_t* rank_dev, int32_t* rrp, int32_t* crp) {
+  const int32_t* PR = c->perm_r.as<int32_t>();
+  const int32_t* PC = c->perm_c.as<int32_t>();
+  if (P && m > 0)
+    PLUQ_CUDA(cudaMemcpyAsync(P, PR, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, c->stream));
+  if (Q && n > 0)
+    PLUQ_CUDA(cudaMemcpyAsync(Q, PC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+  if (rank_dev) {
+    k_store_rank<<<1, 1, 0, c->stream>>>(rank_dev, r);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  if (rrp && r > 0) {
+    k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(m, 32), c->stream>>>(PR, r, m, rrp);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  if (crp && r > 0) {
+    k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(n, 32), c->stream>>>(PC, r, n, crp);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  return PLUQ_OK;
+}
+
+int copy_to_work(pluq_ctx* c, int64_t m, int64_t n, const uint32_t* A, int64_t lda) {
+  PLUQ_TRY(c->work.ensure(sizeof(uint32_t) * std::max<int64_t>(m * n, 1)));
+  if (m > 0 && n > 0) {
+    k_copy_mat<<<grid2(m, n), 256, 0, c->stream>>>(c->work.as<uint32_t>(), n, A, lda, m, n);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  return PLUQ_OK;
+}
+
+}  // namespace
+
+int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
+              const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
+  if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
+  c->n_gemm++;
+  if (c->form == PLUQ_FORM_LIMB_F16) return fgemm_sub_limb(c, M, N, K, A, lda, B, ldb, C, ldc);
+  return fgemm_sub_fp64(c, M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+extern "C" {
+
+int pluq_create(pluq_ctx** ctx, int device) {
+  if (!ctx) return PLUQ_ERR_INVALID_ARG;
+  *ctx = nullptr;
+  pluq_ctx* c = new pluq_ctx();
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return PLUQ_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost(&c->host_small, 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return PLUQ_ERR_CUDA;
+  }
+  *ctx = c;
+  return PLUQ_OK;
+}
+
+int pluq_destroy(pluq_ctx* c) {
+  if (!c) return PLUQ_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  c->scratch.release();
+  c->pack.release();
+  c->perm_r.release();
+  c->perm_c.release();
+  c->tmp_i.release();
+  c->small.release();
+  c->inv_table.release();
+  c->work.release();
+  if (c->host_small) cudaFreeHost(c->host_small);
+  delete c;
+  return PLUQ_OK;
+}
+
+int pluq_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, uint32_t* A, int64_t lda, int32_t* P,
+              int32_t* Q, int64_t* rank_dev, int32_t* rrp, int32_t* crp, int form, void* stream) {
+  if (!c || m < 0 || n < 0 || (m > 0 && !P) || (n > 0 && !Q)) return PLUQ_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && (!A || lda < n)) return PLUQ_ERR_INVALID_ARG;
+  if (m >= 0x7fffffff || n >= 0x7fffffff) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(prepare(c, p, m, n, form, stream));
+  int64_t r = 0;
+  PLUQ_TRY(factor(c, m, n, A, lda, &r));
+  return write_outputs(c, m, n, r, P, Q, rank_dev, rrp, crp);
+}
+
+int rank_profile_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A, int64_t lda,
+                      int64_t* rank_dev, int32_t* rrp, int32_t* crp, int32_t* rpm_col_of_row,
+                      int form, void* stream) {
+  if (!c || m < 0 || n < 0) return PLUQ_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && (!A || lda < n)) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(prepare(c, p, m, n, form, stream));
+  PLUQ_TRY(copy_to_work(c, m, n, A, lda));
+  int64_t r = 0;
+  PLUQ_TRY(factor(c, m, n, c->work.as<uint32_t>(), std::max<int64_t>(n, 1), &r));
+  PLUQ_TRY(write_outputs(c, m, n, r, nullptr, nullptr, rank_dev, rrp, crp));
+  if (rpm_col_of_row && m > 0) {
+    const int32_t* PR = c->perm_r.as<int32_t>();
+    const int32_t* PC = c->perm_c.as<int32_t>();
+    k_rpm_col_of_row<<<(unsigned)cdiv(m, 256), 256, 0, c->stream>>>(PR, PC, r, m, rpm_col_of_row);
+    if (r > 0) k_rpm_fill<<<(unsigned)cdiv(r, 256), 256, 0, c->stream>>>(PR, PC, r, rpm_col_of_row);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  return PLUQ_OK;
+}
+
+int echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A, int64_t lda,
+                 uint32_t* R, int64_t ldr, int64_t* rank_dev, int32_t* crp, int form, void* stream) {
+  if (!c || m < 0 || n < 0) return PLUQ_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && (!A || !R || lda < n || ldr < n)) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(prepare(c, p, m, n, form, stream));
+  PLUQ_TRY(copy_to_work(c, m, n, A, lda));
+  int64_t r = 0;
+  uint32_t* W = c->work.as<uint32_t>();
+  const int64_t ldw = std::max<int64_t>(n, 1);
+  PLUQ_TRY(factor(c, m, n, W, ldw, &r));
+  PLUQ_TRY(write_outputs(c, m, n, r, nullptr, nullptr, rank_dev, nullptr, nullptr));
+  if (r == 0) return PLUQ_OK;
+  // X = U1^{-1} [U1 U2] in the Q frame: only U2 needs solving.
+  PLUQ_TRY(trsm_left_upper(c, W, ldw, r, W + r, ldw, n - r));
+  int32_t* ints = c->tmp_i.as<int32_t>();
+  PLUQ_TRY(c->tmp_i.ensure(sizeof(int32_t) * (n + r + 64)));
+  ints = c->tmp_i.as<int32_t>();
+  int32_t* qinv = ints;
+  int32_t* crp_buf = crp ? crp : ints + n;
+  const int32_t* PC = c->perm_c.as<int32_t>();
+  k_invert_perm<<<(unsigned)cdiv(n, 256), 256, 0, c->stream>>>(PC, n, qinv);
+  k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(n, 32), c->stream>>>(PC, r, n, crp_buf);
+  k_rref_scatter<<<grid2(r, n), 256, 0, c->stream>>>(W, ldw, r, n, qinv, crp_buf, R, ldr);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int fgemm_modp(pluq_ctx* c, uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+               int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc, int form,
+               void* stream) {
+  if (!c || M < 0 || N < 0 || K < 0) return PLUQ_ERR_INVALID_ARG;
+  if (M > 0 && N > 0 && K > 0 && (!A || !B || !C || lda < K || ldb < N || ldc < N))
+    return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(prepare(c, p, M, N, form, stream));
+  return fgemm_sub(c, M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, const int64_t* n,
+                      uint32_t* const* A, const int64_t* lda, int32_t* const* P, int32_t* const* Q,
+                      int64_t* ranks, int32_t* status, int form, void* stream) {
+  if (!c || batch < 0 || (batch > 0 && (!m || !n || !A || !lda || !P || !Q || !ranks)))
+    return PLUQ_ERR_INVALID_ARG;
+  int first = PLUQ_OK;
+  for (int32_t b = 0; b < batch; ++b) {
+    int st = pluq_modp(c, p, m[b], n[b], A[b], lda[b], P[b], Q[b], nullptr, nullptr, nullptr, form,
+                       stream);
+    ranks[b] = st == PLUQ_OK ? (int64_t)c->host_small[8] : -1;
+    if (status) status[b] = st;
+    if (st != PLUQ_OK && first == PLUQ_OK) first = st;
+  }
+  return first;
+}
+
+int pluq_last_rank(pluq_ctx* c, int64_t* rank) {
+  if (!c || !rank) return PLUQ_ERR_INVALID_ARG;
+  *rank = c->host_small[8];
+  return PLUQ_OK;
+}
+
+int pluq_set_tuning(pluq_ctx* c, int bm, int bn, int trsm_block) {
+  if (!c) return PLUQ_ERR_INVALID_ARG;
+  if (bm < 0 || bm > 128 || bn < 0 || bn > 128 || trsm_block < 0 || trsm_block > 64)
+    return PLUQ_ERR_INVALID_ARG;
+  if (bm) c->bm = bm;
+  if (bn) c->bn = bn;
+  if (trsm_block) c->trsm_block = trsm_block;
+  return PLUQ_OK;
+}
+
+int pluq_last_stats(pluq_ctx* c, int64_t* n_base, int64_t* n_nodes, int64_t* n_gemm) {
+  if (!c) return PLUQ_ERR_INVALID_ARG;
+  if (n_base) *n_base = c->n_base;
+  if (n_nodes) *n_nodes = c->n_nodes;
+  if (n_gemm) *n_gemm = c->n_gemm;
+  return PLUQ_OK;
+}
+
+const char* pluq_status_string(int s) {
+  switch (s) {
+    case PLUQ_OK: return "ok";
+    case PLUQ_ERR_INVALID_ARG: return "invalid argument";
+    case PLUQ_ERR_P_NOT_PRIME: return "p is not prime";
+    case PLUQ_ERR_P_OUT_OF_RANGE: return "p out of range [2, 2^31)";
+    case PLUQ_ERR_ENTRY_OUT_OF_RANGE: return "matrix entry >= p";
+    case PLUQ_ERR_UNSUPPORTED_FORM: return "fgemm form unsupported for this p";
+    case PLUQ_ERR_NO_WORKSPACE: return "device workspace allocation failed";
+    case PLUQ_ERR_CUDA: return "CUDA error";
+    case PLUQ_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

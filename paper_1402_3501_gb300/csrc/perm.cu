@@ -1,0 +1,165 @@
+// Permutation kernels of the recursion (the flaswp of Sec. 2.1 / Sec. 2.3):
+// row and column gathers of rectangular blocks, composition of index vectors
+// and the block-cyclic shifts that gather the pivots of the four recursive
+// calls at the front of a block.
+//
+// A block permutation is applied out of place into the context scratch (one
+// coalesced read and write per element) and copied back, because the
+// permutations of the recursion are arbitrary (pivots interleaved with the
+// rest) and in-place cycle following does not vectorise.
+#include "common.cuh"
+
+namespace {
+
+__global__ void k_iota(int32_t* __restrict__ dst, int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (int32_t)i;
+}
+
+// base[t] = base[perm[t]], t < count, through shared memory (count small).
+__global__ void k_compose_smem(int32_t* __restrict__ base, const int32_t* __restrict__ perm,
+                               int count) {
+  extern __shared__ int32_t s[];
+  for (int t = threadIdx.x; t < count; t += blockDim.x) s[t] = base[perm[t]];
+  __syncthreads();
+  for (int t = threadIdx.x; t < count; t += blockDim.x) base[t] = s[t];
+}
+
+__global__ void k_compose_gather(int32_t* __restrict__ out, const int32_t* __restrict__ base,
+                                 const int32_t* __restrict__ perm, int64_t count) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) out[t] = base[perm[t]];
+}
+
+__global__ void k_copy_i32(int32_t* __restrict__ dst, const int32_t* __restrict__ src,
+                           int64_t count) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = src[t];
+}
+
+struct Segs {
+  int64_t start[4];
+  int64_t len[4];
+  int n;
+};
+
+__global__ void k_segperm(int32_t* __restrict__ out, Segs sg, int64_t total) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int64_t acc = 0;
+  for (int k = 0; k < sg.n; ++k) {
+    if (t < acc + sg.len[k]) {
+      out[t] = (int32_t)(sg.start[k] + (t - acc));
+      return;
+    }
+    acc += sg.len[k];
+  }
+}
+
+// dst[t, :] = src[perm[t], :] (rows x cols)
+__global__ void k_gather_rows(uint32_t* __restrict__ dst, int64_t ldd,
+                              const uint32_t* __restrict__ src, int64_t lds, int64_t rows,
+                              int64_t cols, const int32_t* __restrict__ perm) {
+  for (int64_t t = blockIdx.y; t < rows; t += gridDim.y) {
+    const uint32_t* s = src + (int64_t)perm[t] * lds;
+    uint32_t* d = dst + t * ldd;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
+         u += (int64_t)gridDim.x * blockDim.x)
+      d[u] = s[u];
+  }
+}
+
+// dst[t, u] = src[t, perm[u]]
+__global__ void k_gather_cols(uint32_t* __restrict__ dst, int64_t ldd,
+                              const uint32_t* __restrict__ src, int64_t lds, int64_t rows,
+                              int64_t cols, const int32_t* __restrict__ perm) {
+  for (int64_t t = blockIdx.y; t < rows; t += gridDim.y) {
+    const uint32_t* s = src + t * lds;
+    uint32_t* d = dst + t * ldd;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
+         u += (int64_t)gridDim.x * blockDim.x)
+      d[u] = s[perm[u]];
+  }
+}
+
+__global__ void k_copy2d(uint32_t* __restrict__ dst, int64_t ldd, const uint32_t* __restrict__ src,
+                         int64_t lds, int64_t rows, int64_t cols) {
+  for (int64_t t = blockIdx.y; t < rows; t += gridDim.y) {
+    const uint32_t* s = src + t * lds;
+    uint32_t* d = dst + t * ldd;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
+         u += (int64_t)gridDim.x * blockDim.x)
+      d[u] = s[u];
+  }
+}
+
+dim3 grid2d(int64_t rows, int64_t cols, int threads) {
+  int64_t gx = cdiv(cols, threads);
+  if (gx > 64) gx = 64;
+  int64_t gy = rows;
+  if (gy > 65535) gy = 65535;
+  return dim3((unsigned)gx, (unsigned)gy, 1);
+}
+
+}  // namespace
+
+int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count) {
+  if (count <= 0) return PLUQ_OK;
+  k_iota<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(dst, count);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t count) {
+  if (count <= 1) return PLUQ_OK;
+  if (count <= 12288) {
+    k_compose_smem<<<1, 1024, sizeof(int32_t) * count, c->stream>>>(base, perm, (int)count);
+  } else {
+    PLUQ_TRY(c->tmp_i.ensure(sizeof(int32_t) * count));
+    int32_t* tmp = c->tmp_i.as<int32_t>();
+    k_compose_gather<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(tmp, base, perm, count);
+    k_copy_i32<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(base, tmp, count);
+  }
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const int64_t* seg_len,
+                   int nseg) {
+  Segs sg{};
+  int64_t total = 0;
+  sg.n = nseg;
+  for (int k = 0; k < nseg; ++k) {
+    sg.start[k] = seg_start[k];
+    sg.len[k] = seg_len[k];
+    total += seg_len[k];
+  }
+  if (total <= 0) return PLUQ_OK;
+  k_segperm<<<(unsigned)cdiv(total, 256), 256, 0, c->stream>>>(out, sg, total);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
+                 const int32_t* perm) {
+  if (rows <= 1 || cols <= 0) return PLUQ_OK;
+  PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
+  uint32_t* S = c->scratch.as<uint32_t>();
+  const dim3 g = grid2d(rows, cols, 256);
+  k_gather_rows<<<g, 256, 0, c->stream>>>(S, cols, A, lda, rows, cols, perm);
+  k_copy2d<<<g, 256, 0, c->stream>>>(A, lda, S, cols, rows, cols);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int permute_cols(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
+                 const int32_t* perm) {
+  if (rows <= 0 || cols <= 1) return PLUQ_OK;
+  PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
+  uint32_t* S = c->scratch.as<uint32_t>();
+  const dim3 g = grid2d(rows, cols, 256);
+  k_gather_cols<<<g, 256, 0, c->stream>>>(S, cols, A, lda, rows, cols, perm);
+  k_copy2d<<<g, 256, 0, c->stream>>>(A, lda, S, cols, rows, cols);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}

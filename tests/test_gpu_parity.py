@@ -1,0 +1,290 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact on every seeded input: rank, rank profile matrix (pivots of P, Q),
+row and column rank profiles, reduced echelon form, and the factor identity
+P L U Q = A mod p with the library's storage conventions.  Sizes span several
+base-case tiles with ragged tails; the recursion is also driven deep with
+small tiles so every block of the recursion (F, G, H, R, shifts) is exercised.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from pluq_checks import check_pluq, check_rpm_from_pq, check_rref, matmul_mod
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only containers
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1402_3501_gb300 as pq  # noqa: E402
+
+FORMS = ["fp64", "auto"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pq.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(A):
+    return torch.from_numpy(np.ascontiguousarray(A).astype(np.int32)).cuda()
+
+
+def run_pluq(ctx, A, p, form):
+    res = pq.pluq_modp(to_dev(A), p, form=form, ctx=ctx)
+    torch.cuda.synchronize()
+    return (res.rank, res.P.cpu().numpy(), res.Q.cpu().numpy(), res.LU.cpu().numpy(),
+            res.rrp.cpu().numpy(), res.crp.cpu().numpy())
+
+
+def assert_parity(ctx, A, p, form="auto", expect=None):
+    r, P, Q, LU, rrp, crp = run_pluq(ctx, A, p, form)
+    ref = oracle.pluq(A, p) if expect is None else expect
+    assert r == ref.rank
+    check_rpm_from_pq(P, Q, r, ref.rpm)
+    assert rrp.tolist() == ref.rrp.tolist()
+    assert crp.tolist() == ref.crp.tolist()
+    check_pluq(A, p, P, Q, LU.astype(np.int64), r)
+    return r
+
+
+# ---------------------------------------------------------------- fgemm ----
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p", [2, 3, 251, 65521, 131071])
+@pytest.mark.parametrize("mnk", [(1, 1, 1), (70, 33, 17), (129, 257, 100), (300, 200, 700),
+                                 (64, 64, 1024)])
+def test_fgemm_parity(ctx, form, p, mnk):
+    M, N, K = mnk
+    rng = np.random.default_rng(M * 7 + N * 3 + K + p % 97)
+    A = rng.integers(0, p, (M, K), dtype=np.int64)
+    B = rng.integers(0, p, (K, N), dtype=np.int64)
+    C = rng.integers(0, p, (M, N), dtype=np.int64)
+    expect = (C - matmul_mod(A, B, p)) % p
+    Cd = to_dev(C)
+    pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form=form, ctx=ctx)
+    torch.cuda.synchronize()
+    assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_fgemm_adversarial_extremes(ctx, form):
+    # all entries p-1: the largest products the delayed reduction must absorb
+    for p in [65521, 131071]:
+        for K in [255, 256, 257, 1024, 4099]:
+            A = np.full((130, K), p - 1, dtype=np.int64)
+            B = np.full((K, 70), p - 1, dtype=np.int64)
+            C = np.zeros((130, 70), dtype=np.int64)
+            expect = (C - matmul_mod(A, B, p)) % p
+            Cd = to_dev(C)
+            pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form=form, ctx=ctx)
+            torch.cuda.synchronize()
+            assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), (p, K)
+
+
+def test_fgemm_strided_views(ctx):
+    p = 131071
+    rng = np.random.default_rng(3)
+    big = to_dev(rng.integers(0, p, (300, 400)))
+    A = big[10:110, 5:77]
+    B = big[120:192, 200:333]
+    C = big[200:300, 0:133].clone()
+    expect = (C.cpu().numpy().astype(np.int64)
+              - matmul_mod(A.cpu().numpy(), B.cpu().numpy(), p)) % p
+    pq.fgemm_modp(C, A, B, p, ctx=ctx)
+    torch.cuda.synchronize()
+    assert np.array_equal(C.cpu().numpy().astype(np.int64), expect)
+
+
+# ------------------------------------------------------------- pluq ----
+
+SHAPES = [(1, 1), (1, 40), (40, 1), (17, 33), (128, 128), (129, 130), (200, 300), (300, 200),
+          (513, 257)]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p", [2, 3, 65521, 131071])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_pluq_uniform(ctx, form, p, shape):
+    m, n = shape
+    A = workloads.uniform_matrix(m, n, p, seed=1)
+    assert_parity(ctx, A, p, form)
+
+
+@pytest.mark.parametrize("p", [3, 131071])
+@pytest.mark.parametrize("shape", [(64, 64), (150, 200), (300, 260), (513, 257), (700, 700)])
+@pytest.mark.parametrize("frac", [0.0, 0.1, 0.5, 0.9])
+def test_pluq_prescribed_rank(ctx, p, shape, frac):
+    m, n = shape
+    r = int(min(m, n) * frac)
+    g = workloads.prescribed_rank_matrix(m, n, r, p, seed=2)
+    got = assert_parity(ctx, g.A, p)
+    assert got == r
+
+
+@pytest.mark.parametrize("tiles", [(8, 8), (16, 8), (5, 13), (32, 32), (128, 64)])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_pluq_deep_recursion(ctx, tiles, seed):
+    # small base tiles drive many recursion levels through every block step
+    p = 131071
+    ctx.set_tuning(tiles[0], tiles[1], 0)
+    try:
+        for m, n, frac in [(90, 70, 0.5), (64, 100, 0.3), (133, 133, 1.0)]:
+            g = workloads.prescribed_rank_matrix(m, n, int(min(m, n) * frac), p, seed)
+            assert_parity(ctx, g.A, p)
+        A = workloads.uniform_matrix(77, 91, 5, seed)
+        assert_parity(ctx, A, 5)
+    finally:
+        ctx.set_tuning(128, 128, 0)
+
+
+@pytest.mark.parametrize("tb", [1, 7, 16, 64])
+def test_pluq_trsm_blocks(ctx, tb):
+    p = 65521
+    ctx.set_tuning(32, 32, tb)
+    try:
+        g = workloads.prescribed_rank_matrix(260, 240, 180, p, seed=4)
+        assert_parity(ctx, g.A, p)
+    finally:
+        ctx.set_tuning(128, 128, 64)
+
+
+def test_pluq_special_matrices(ctx):
+    p = 131071
+    for n in [1, 5, 129, 300]:
+        assert_parity(ctx, np.eye(n, dtype=np.uint32), p)
+        assert_parity(ctx, np.zeros((n, n + 7), dtype=np.uint32), p)
+        perm = np.random.default_rng(n).permutation(n)
+        Pm = np.zeros((n, n), dtype=np.uint32)
+        Pm[np.arange(n), perm] = 1
+        assert_parity(ctx, Pm, p)
+    u = np.arange(1, 301, dtype=np.int64)
+    v = np.arange(7, 207, dtype=np.int64)
+    u[:50] = 0
+    v[:120] = 0
+    assert_parity(ctx, matmul_mod(u[:, None], v[None, :], p).astype(np.uint32), p)
+
+
+def test_pluq_strided_lda(ctx):
+    p = 131071
+    g = workloads.prescribed_rank_matrix(200, 150, 90, p, seed=7)
+    big = torch.zeros((200, 180), dtype=torch.int32, device="cuda")
+    big[:, :150] = to_dev(g.A)
+    big[:, 150:] = 12345
+    view = big[:, :150]
+    res = pq.pluq_modp(view, p, ctx=ctx)
+    torch.cuda.synchronize()
+    assert res.rank == 90
+    assert torch.all(big[:, 150:] == 12345)
+    check_pluq(g.A, p, res.P.cpu().numpy(), res.Q.cpu().numpy(),
+               view.cpu().numpy().astype(np.int64), res.rank)
+    check_rpm_from_pq(res.P.cpu().numpy(), res.Q.cpu().numpy(), 90, g.rpm)
+
+
+def test_pluq_empty(ctx):
+    for shape in [(0, 5), (5, 0), (0, 0)]:
+        A = torch.zeros(shape, dtype=torch.int32, device="cuda")
+        res = pq.pluq_modp(A, 131071, ctx=ctx)
+        assert res.rank == 0
+        assert res.P.cpu().tolist() == list(range(shape[0]))
+        assert res.Q.cpu().tolist() == list(range(shape[1]))
+
+
+# ----------------------------------------------------- echelon / profiles --
+
+@pytest.mark.parametrize("p", [3, 65521, 131071])
+@pytest.mark.parametrize("shape,frac", [((40, 60), 0.5), ((257, 300), 0.7), ((300, 257), 1.0),
+                                        ((129, 129), 0.0)])
+def test_echelon_parity(ctx, p, shape, frac):
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(min(m, n) * frac), p, seed=5)
+    r, R, crp = pq.echelon_modp(to_dev(g.A), p, ctx=ctx)
+    torch.cuda.synchronize()
+    rr, Rref = oracle.rref(g.A, p)
+    assert r == rr == g.rank
+    assert crp.cpu().tolist() == g.crp.tolist()
+    assert np.array_equal(R.cpu().numpy().astype(np.int64), Rref.astype(np.int64))
+    check_rref(g.A, p, R.cpu().numpy(), crp.cpu().numpy())
+
+
+@pytest.mark.parametrize("p", [2, 131071])
+def test_rank_profile_parity(ctx, p):
+    g = workloads.prescribed_rank_matrix(333, 222, 111, p, seed=6)
+    A = to_dev(g.A)
+    before = A.clone()
+    r, rrp, crp, rpm = pq.rank_profile_modp(A, p, ctx=ctx)
+    torch.cuda.synchronize()
+    assert torch.equal(A, before)
+    assert r == g.rank
+    assert rrp.cpu().tolist() == g.rrp.tolist()
+    assert crp.cpu().tolist() == g.crp.tolist()
+    expect = np.full(333, -1)
+    expect[g.rows] = g.cols
+    assert rpm.cpu().numpy().tolist() == expect.tolist()
+
+
+# ------------------------------------------------------------- errors --
+
+def test_status_codes(ctx):
+    A = to_dev(np.ones((4, 4)))
+    with pytest.raises(pq.PluqError) as e:
+        pq.pluq_modp(A.clone(), 15, ctx=ctx)
+    assert e.value.status == -2
+    with pytest.raises(pq.PluqError) as e:
+        pq.pluq_modp(A.clone(), 2 ** 31 + 11, ctx=ctx)
+    assert e.value.status == -3
+    bad = to_dev(np.full((4, 4), 7))
+    keep = bad.clone()
+    with pytest.raises(pq.PluqError) as e:
+        pq.pluq_modp(bad, 5, ctx=ctx)
+    assert e.value.status == -4
+    assert torch.equal(bad, keep)
+    # the context stays usable after errors
+    assert_parity(ctx, workloads.uniform_matrix(50, 50, 131071, 1), 131071)
+
+
+# ------------------------------------------------ workload-size parity --
+
+def test_config_uniform_1024(ctx):
+    cfg = workloads.CONFIGS["uniform-1024-p131071"]
+    for seed in (1, 2):
+        A = workloads.uniform_matrix(cfg.m, cfg.n, cfg.p, seed)
+        assert_parity(ctx, A, cfg.p, "auto")
+        assert_parity(ctx, A, cfg.p, "fp64")
+
+
+def freivalds(A, p, P, Q, LU, r, trials=2, seed=0):
+    """Random-vector check of A[P][:, Q] = L U mod p (error < p^-trials)."""
+    rng = np.random.default_rng(seed)
+    m, n = A.shape
+    A64 = A.astype(np.int64)
+    L = LU[:, :r].astype(np.int64)
+    U = LU[:r, :].astype(np.int64)
+    for _ in range(trials):
+        x = rng.integers(0, p, n, dtype=np.int64)
+        z = np.zeros(n, dtype=np.int64)
+        z[Q] = x  # (A Q^T x)  = A z
+        lhs = (A64 @ z % p)[P] if p < 2 ** 20 else matmul_mod(A64, z[:, None], p)[:, 0][P]
+        ux = np.triu(U) @ x % p if p < 2 ** 20 else matmul_mod(np.triu(U), x[:, None], p)[:, 0]
+        Lt = np.tril(L, -1)
+        Lt[np.arange(r), np.arange(r)] = 1
+        rhs = (Lt @ ux) % p if p < 2 ** 20 else matmul_mod(Lt, ux[:, None], p)[:, 0]
+        assert np.array_equal(lhs % p, rhs), "Freivalds check of P L U Q = A failed"
+
+
+@pytest.mark.parametrize("form", ["auto", "fp64"])
+def test_config_lru_8192(ctx, form):
+    cfg = workloads.CONFIGS["lru-8192-r4096-p131071"]
+    g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
+    r, P, Q, LU, rrp, crp = run_pluq(ctx, g.A, cfg.p, form)
+    assert r == cfg.r
+    check_rpm_from_pq(P, Q, r, g.rpm)
+    assert rrp.tolist() == g.rrp.tolist() and crp.tolist() == g.crp.tolist()
+    assert not np.any(LU[r:, r:])
+    assert np.all(np.diag(LU[:r, :r]) != 0)
+    freivalds(g.A, cfg.p, P, Q, LU, r)
