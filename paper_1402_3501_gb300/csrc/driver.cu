@@ -215,10 +215,12 @@ struct Recursion {
     if (m <= c->bm && n <= c->bn) {
       c->n_base++;
       PLUQ_TRY(launch_base_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
-      PLUQ_CUDA(cudaMemcpyAsync(c->host_small, rank_slot, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                c->stream));
+      // rank (int 8 of the scalar block) and the device error word (int 16)
+      PLUQ_CUDA(cudaMemcpyAsync(c->host_small, c->small.ptr, 32 * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
       PLUQ_CUDA(cudaStreamSynchronize(c->stream));
-      *r_out = c->host_small[0];
+      if (c->host_small[16] != 0) return c->host_small[16];
+      *r_out = c->host_small[8];
       return PLUQ_OK;
     }
     if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
@@ -347,6 +349,12 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
   PLUQ_TRY(c->tmp_i.ensure(sizeof(int32_t) * std::max(c->mmax, c->nmax)));
   PLUQ_TRY(c->small.ensure(256));
   PLUQ_TRY(ensure_inv_table(c));
+  if (c->form == PLUQ_FORM_LIMB_F16) {
+    // digit planes of the largest fgemm operands (K <= min(m, n) / 2 + 64)
+    const int64_t kp = cdiv(std::min(m, n) / 2 + 64, 64) * 64;
+    const int64_t rows = cdiv(m, 128) * 128 + cdiv(n, 128) * 128;
+    PLUQ_TRY(c->pack.ensure(sizeof(uint16_t) * 2 * rows * kp + 4096));
+  }
   int* flag = c->small.as<int>();
   PLUQ_CUDA(cudaMemsetAsync(flag, 0, 256, c->stream));
   if (m > 0 && n > 0) {
@@ -358,6 +366,10 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
   }
   Recursion rec{c, A, lda, c->small.as<int32_t>() + 8};
   PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out));
+  PLUQ_CUDA(cudaMemcpyAsync(c->host_small, c->small.ptr, 32 * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, c->stream));
+  PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->host_small[16] != 0) return c->host_small[16];
   c->host_small[8] = (int32_t)*r_out;
   return PLUQ_OK;
 }
@@ -508,6 +520,8 @@ int fgemm_modp(pluq_ctx* c, uint32_t p, int64_t M, int64_t N, int64_t K, const u
   if (M > 0 && N > 0 && K > 0 && (!A || !B || !C || lda < K || ldb < N || ldc < N))
     return PLUQ_ERR_INVALID_ARG;
   PLUQ_TRY(prepare(c, p, M, N, form, stream));
+  PLUQ_TRY(c->small.ensure(256));
+  PLUQ_CUDA(cudaMemsetAsync(c->small.ptr, 0, 256, c->stream));
   return fgemm_sub(c, M, N, K, A, lda, B, ldb, C, ldc);
 }
 

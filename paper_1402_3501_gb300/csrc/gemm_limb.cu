@@ -1,13 +1,556 @@
-// fgemm, limb form (tcgen05 tensor cores): placeholder until the kernel lands.
+// fgemm, limb form: C <- C - A B mod p on the tcgen05 tensor cores.
+//
+// Delayed modular reduction (Sec. 3.1) needs products summed exactly; the
+// paper does it in the 53-bit mantissa of doubles.  Here the residues are
+// balanced to |x| <= (p-1)/2 and split into L signed base-2^8 digits
+// (x = sum_l d_l 2^{8l}), each held exactly in FP16.  One tcgen05.mma
+// kind::f16 per digit pair accumulates into FP32 in tensor memory (TMEM);
+// products of equal weight 2^{8w} share one accumulator (2L-1 of them).  An
+// FP32 accumulator is exact while every partial sum stays within 2^24, so a
+// block of at most k_flush = floor(2^24 / max weight-class product) columns of
+// K is accumulated before the epilogue warps drain the accumulators:
+// t = sum_w c_w 2^{8w} (int64, exact), reduced mod p by one Montgomery step
+// and added to a residue kept in TMEM.  The last drain writes C - residue.
+//
+// Structure (one CTA per 128 x 128 tile of C, warp-specialised):
+//   warp 0     TMA producer: digit planes of A (128 x 64 FP16, 128B swizzle)
+//              and of B^T into a 3-stage shared-memory ring;
+//   warp 1     TMEM allocation and the single MMA-issuing thread;
+//   warps 2-9  epilogue: two warps per TMEM lane quadrant, 64 columns each.
+// The digit planes are written by a packing pass into workspace.  Every
+// mbarrier wait is bounded; on expiry the kernel records PLUQ_ERR_TIMEOUT in
+// the error word, drains, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+
 #include "common.cuh"
 
-int limb_form_supported(uint32_t p) {
-  (void)p;
-  return 0;
+namespace {
+
+constexpr int kTM = 128, kTN = 128, kTK = 64;  // CTA tile, K block (one 128B swizzle row)
+constexpr int kLimbBits = 8;
+constexpr int kGemmThreads = 320;               // 10 warps
+constexpr int kTileBytes = kTM * kTK * 2;        // 16 KiB per digit plane tile
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------ PTX helpers --
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and the error word set) when the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(err, PLUQ_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups of
+// 1024 B (stride byte offset), descriptor version 1 (tcgen05).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: F32 accumulate, F16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------ the kernel --
+
+template <int L>
+struct LimbCfg {
+  static constexpr int kStages = L == 1 ? 6 : 3;
+  static constexpr int kClasses = 2 * L - 1;
+  static constexpr int kStageBytes = 2 * L * kTileBytes;
+  static constexpr int kResCol = kClasses * kTN;  // residue columns in TMEM
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+};
+
+template <int L>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_fgemm_limb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 int64_t M, int64_t N, int Mp, int Np, int num_kb, int group_kb,
+                 uint32_t* __restrict__ C, int64_t ldc, FieldP F, uint64_t bias,
+                 int* __restrict__ err) {
+  using Cfg = LimbCfg<L>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* full = bars;                      // [kStages]
+  uint64_t* empty = bars + Cfg::kStages;      // [kStages]
+  uint64_t* acc_full = bars + 2 * Cfg::kStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* mma_done = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int num_groups = (num_kb + group_kb - 1) / group_kb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------- TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % Cfg::kStages;
+        const uint32_t ph = (kb / Cfg::kStages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, err)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        mbar_expect_tx(&full[s], Cfg::kStageBytes);
+        const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          tma_load_2d(st + l * kTileBytes, &tmA, kb * kTK, l * Mp + m0, &full[s]);
+          tma_load_2d(st + (L + l) * kTileBytes, &tmB, kb * kTK, l * Np + n0, &full[s]);
+        }
+        issued = kb + 1;
+      }
+      // drain: every issued copy lands before the CTA may exit
+      for (int kb = (issued > Cfg::kStages ? issued - Cfg::kStages : 0); kb < issued; ++kb)
+        mbar_wait(&full[kb % Cfg::kStages], (kb / Cfg::kStages) & 1, err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------- MMA issuer
+      const uint32_t tacc[3] = {tmem, tmem + (uint32_t)kTN, tmem + 2u * kTN};
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % Cfg::kStages;
+        const int g = kb / group_kb;
+        const bool first = (kb % group_kb) == 0;
+        const bool last = (kb % group_kb) == group_kb - 1 || kb == num_kb - 1;
+        if (first && g > 0) {
+          if (!mbar_wait(acc_empty, (g - 1) & 1, err)) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+        if (!mbar_wait(&full[s], (kb / Cfg::kStages) & 1, err)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < kTK / 16; ++kk) {
+          const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+          uint64_t da[L], db[L];
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            da[l] = smem_desc_sw128(st + l * kTileBytes + kk * 32);
+            db[l] = smem_desc_sw128(st + (L + l) * kTileBytes + kk * 32);
+          }
+          if (L == 1) {
+            umma_f16(tacc[0], da[0], db[0], acc);
+          } else {
+            umma_f16(tacc[0], da[0], db[0], acc);
+            umma_f16(tacc[1], da[0], db[1 % L], acc);
+            umma_f16(tacc[1], da[1 % L], db[0], 1u);
+            umma_f16(tacc[2], da[1 % L], db[1 % L], acc);
+          }
+        }
+        umma_commit(&empty[s]);
+        if (last) umma_commit(acc_full);
+      }
+      // every issued MMA completes before TMEM is released
+      umma_commit(mma_done);
+      mbar_wait(mma_done, 0, err);
+    }
+  } else {
+    // -------------------------------------------------------- epilogue
+    const int q = warp & 3;           // TMEM lane quadrant of this warp
+    const int h = (warp - 2) >> 2;    // column half
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    const int64_t grow = (int64_t)m0 + row;
+    for (int g = 0; g < num_groups; ++g) {
+      if (!mbar_wait(acc_full, g & 1, err)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const bool last_group = g == num_groups - 1;
+#pragma unroll 1
+      for (int ch = 0; ch < 4; ++ch) {
+        const int col = h * 64 + ch * 16;
+        uint32_t c0[16], c1[16], c2[16], res[16];
+        tmem_ld16(lane_base + col, c0);
+        if (L == 2) {
+          tmem_ld16(lane_base + kTN + col, c1);
+          tmem_ld16(lane_base + 2 * kTN + col, c2);
+        }
+        if (g > 0) tmem_ld16(lane_base + Cfg::kResCol + col, res);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          int64_t t = (int64_t)__float2int_rn(__uint_as_float(c0[e]));
+          if (L == 2) {
+            t += (int64_t)__float2int_rn(__uint_as_float(c1[e])) * (1 << kLimbBits);
+            t += (int64_t)__float2int_rn(__uint_as_float(c2[e])) * (1 << (2 * kLimbBits));
+          }
+          const uint32_t v = F.is2 ? (uint32_t)((uint64_t)(t + (int64_t)bias) & 1u)
+                                   : f_redc((uint64_t)(t + (int64_t)bias), F);
+          res[e] = g > 0 ? f_add(res[e], v, F) : v;
+        }
+        if (!last_group) {
+          tmem_st16(lane_base + Cfg::kResCol + col, res);
+        } else if (grow < M) {
+          uint32_t* crow = C + grow * ldc;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int64_t gc = (int64_t)n0 + col + e;
+            if (gc < N) {
+              // residue holds (sum t) R^{-1}; one more step with R^2 undoes it
+              const uint32_t fin = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
+              crow[gc] = f_sub(crow[gc], fin, F);
+            }
+          }
+        }
+      }
+      if (!last_group) {
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// Digit planes of A (M x K) in K-major layout: out[l][i][k], rows padded to
+// Mp and columns to Kp with zeros.
+template <int L>
+__global__ void k_pack_rows(const uint32_t* __restrict__ A, int64_t lda, int64_t M, int64_t K,
+                            int64_t Mp, int64_t Kp, uint32_t p, __half* __restrict__ out) {
+  const int64_t half_p = (p - 1) / 2;
+  for (int64_t i = blockIdx.y; i < Mp; i += gridDim.y)
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Kp;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = 0;
+    if (i < M && k < K) {
+      const int64_t a = A[i * lda + k];
+      x = (int32_t)(a > half_p ? a - (int64_t)p : a);
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      int32_t d;
+      if (l == L - 1) {
+        d = x;
+      } else {
+        d = ((x + (1 << (kLimbBits - 1))) & ((1 << kLimbBits) - 1)) - (1 << (kLimbBits - 1));
+        x = (x - d) >> kLimbBits;
+      }
+      out[(int64_t)l * Mp * Kp + i * Kp + k] = __int2half_rn(d);
+    }
+  }
+}
+
+// Digit planes of B^T: B is K x N row-major; out[l][j][k] (K-major rows of
+// B^T), padded to Np x Kp.  32 x 32 tiles transposed through shared memory.
+template <int L>
+__global__ void k_pack_cols(const uint32_t* __restrict__ B, int64_t ldb, int64_t K, int64_t N,
+                            int64_t Np, int64_t Kp, uint32_t p, __half* __restrict__ out) {
+  __shared__ int32_t tile[32][33];
+  const int64_t k0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t half_p = (p - 1) / 2;
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t k = k0 + yy, j = j0 + tx;
+    int32_t x = 0;
+    if (k < K && j < N) {
+      const int64_t b = B[k * ldb + j];
+      x = (int32_t)(b > half_p ? b - (int64_t)p : b);
+    }
+    tile[yy][tx] = x;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t j = j0 + yy, k = k0 + tx;
+    if (j >= Np || k >= Kp) continue;
+    int32_t x = tile[tx][yy];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      int32_t d;
+      if (l == L - 1) {
+        d = x;
+      } else {
+        d = ((x + (1 << (kLimbBits - 1))) & ((1 << kLimbBits) - 1)) - (1 << (kLimbBits - 1));
+        x = (x - d) >> kLimbBits;
+      }
+      out[(int64_t)l * Np * Kp + j * Kp + k] = __int2half_rn(d);
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side --
+
+struct LimbPlan {
+  int L = 0;
+  int group_kb = 0;  // K blocks of 64 per exact accumulation group
+  uint64_t bias = 0;
+};
+
+// Largest |digit| of each of the L digits over all balanced residues.
+void digit_bounds(uint32_t p, int L, int64_t* bound) {
+  const int64_t h = p / 2;  // balanced residues lie in [-(p/2), p/2] (p = 2: {-1, 0})
+  for (int l = 0; l < L; ++l) bound[l] = 0;
+  auto digits = [&](int64_t x) {
+    for (int l = 0; l < L; ++l) {
+      int64_t d;
+      if (l == L - 1) {
+        d = x;
+      } else {
+        d = ((x + (1 << (kLimbBits - 1))) & ((1 << kLimbBits) - 1)) - (1 << (kLimbBits - 1));
+        x = (x - d) >> kLimbBits;
+      }
+      const int64_t a = d < 0 ? -d : d;
+      if (a > bound[l]) bound[l] = a;
+    }
+  };
+  // low digits never exceed 2^(s-1); the top digit is monotone in x, so its
+  // extremes sit at x = +-h (checked with a window for the rounding carry)
+  const int64_t span = L == 1 ? 0 : (int64_t)1 << (kLimbBits * (L - 1));
+  for (int64_t x = h - span; x <= h; ++x)
+    if (x >= -h) digits(x);
+  for (int64_t x = -h; x <= -h + span; ++x)
+    if (x <= h) digits(x);
+}
+
+LimbPlan plan_for(uint32_t p) {
+  LimbPlan pl;
+  for (int L = 1; L <= 2; ++L) {
+    int64_t b[2] = {0, 0};
+    digit_bounds(p, L, b);
+    // weight-class bounds: class w collects digit pairs (i, w - i)
+    int64_t cls[3] = {0, 0, 0};
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j) cls[i + j] += b[i] * b[j];
+    int64_t worst = 1;
+    for (int w = 0; w < 2 * L - 1; ++w) worst = cls[w] > worst ? cls[w] : worst;
+    const int64_t kmax = ((int64_t)1 << 24) / worst;
+    const int64_t gkb = kmax / kTK;
+    const int64_t need = L == 1 ? 4 : 1;  // L = 1 only when it needs few drains
+    if (gkb < need) continue;
+    const int64_t kflush = gkb * kTK;
+    // largest |t| = sum_w kflush * cls[w] * 2^(8w)
+    long double tmax = 0;
+    for (int w = 0; w < 2 * L - 1; ++w) tmax += (long double)kflush * cls[w] * powl(2.0L, 8 * w);
+    const long double lim = (long double)p * 4294967296.0L;  // REDC input bound p R
+    if (p != 2 && 2 * tmax + p >= lim) continue;
+    pl.L = L;
+    pl.group_kb = (int)(gkb > 1 << 20 ? 1 << 20 : gkb);
+    const uint64_t tm = (uint64_t)tmax + 1;
+    pl.bias = p == 2 ? 0 : (tm + p - 1) / p * p;
+    return pl;
+  }
+  return pl;
+}
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiled get_encode() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(ptr);
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t kp) {
+  EncodeTiled enc = get_encode();
+  if (!enc) return PLUQ_ERR_CUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? PLUQ_OK : PLUQ_ERR_CUDA;
+}
+
+template <int L>
+int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+             int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
+  using Cfg = LimbCfg<L>;
+  static bool attr = false;
+  if (!attr) {
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Cfg::kSmem));
+    attr = true;
+  }
+  const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, kTN) * kTN, Kp = cdiv(K, kTK) * kTK;
+  if (L * Mp > INT32_MAX || L * Np > INT32_MAX || Kp > INT32_MAX) return PLUQ_ERR_INVALID_ARG;
+  const size_t abytes = sizeof(__half) * L * Mp * Kp, bbytes = sizeof(__half) * L * Np * Kp;
+  PLUQ_TRY(c->pack.ensure(abytes + bbytes + 1024));
+  __half* Ap = c->pack.as<__half>();
+  __half* Bp = reinterpret_cast<__half*>(reinterpret_cast<char*>(Ap) + ((abytes + 1023) / 1024) * 1024);
+  {
+    dim3 g((unsigned)std::min<int64_t>(cdiv(Kp, 256), 64), (unsigned)std::min<int64_t>(Mp, 65535));
+    k_pack_rows<L><<<g, 256, 0, c->stream>>>(A, lda, M, K, Mp, Kp, c->F.p, Ap);
+    dim3 g2((unsigned)cdiv(Kp, 32), (unsigned)cdiv(Np, 32));
+    k_pack_cols<L><<<g2, dim3(32, 8), 0, c->stream>>>(B, ldb, K, N, Np, Kp, c->F.p, Bp);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  CUtensorMap ma, mb;
+  PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp));
+  PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp));
+  const dim3 grid((unsigned)(Np / kTN), (unsigned)(Mp / kTM));
+  if (grid.y > 65535 || cdiv(Np, 32) > 65535) return PLUQ_ERR_INVALID_ARG;
+  int* err = c->small.as<int>() + 16;
+  k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, c->stream>>>(
+      ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK), pl.group_kb, C, ldc, c->F, pl.bias, err);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+}  // namespace
+
+int limb_form_supported(uint32_t p) { return plan_for(p).L > 0; }
 
 int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
                    const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
-  (void)c; (void)M; (void)N; (void)K; (void)A; (void)lda; (void)B; (void)ldb; (void)C; (void)ldc;
+  if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
+  static uint32_t cached_p = 0;
+  static LimbPlan cached;
+  if (cached_p != c->F.p) {
+    cached = plan_for(c->F.p);
+    cached_p = c->F.p;
+  }
+  if (cached.L == 1) return run_limb<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  if (cached.L == 2) return run_limb<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   return PLUQ_ERR_UNSUPPORTED_FORM;
 }

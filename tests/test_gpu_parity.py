@@ -21,7 +21,7 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU-only containers
 
 import paper_1402_3501_gb300 as pq  # noqa: E402
 
-FORMS = ["fp64", "auto"]
+FORMS = ["fp64", "limb"]
 
 
 @pytest.fixture(scope="module")
@@ -85,6 +85,15 @@ def test_fgemm_adversarial_extremes(ctx, form):
             pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form=form, ctx=ctx)
             torch.cuda.synchronize()
             assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), (p, K)
+
+
+def test_fgemm_unsupported_forms(ctx):
+    p = 2147483647
+    A = to_dev(np.ones((8, 8)))
+    for form in ["fp64", "limb", "auto"]:
+        with pytest.raises(pq.PluqError) as e:
+            pq.fgemm_modp(A.clone(), A, A, p, form=form, ctx=ctx)
+        assert e.value.status == -5
 
 
 def test_fgemm_strided_views(ctx):
@@ -254,7 +263,7 @@ def test_config_uniform_1024(ctx):
     cfg = workloads.CONFIGS["uniform-1024-p131071"]
     for seed in (1, 2):
         A = workloads.uniform_matrix(cfg.m, cfg.n, cfg.p, seed)
-        assert_parity(ctx, A, cfg.p, "auto")
+        assert_parity(ctx, A, cfg.p, "limb")
         assert_parity(ctx, A, cfg.p, "fp64")
 
 
@@ -277,7 +286,7 @@ def freivalds(A, p, P, Q, LU, r, trials=2, seed=0):
         assert np.array_equal(lhs % p, rhs), "Freivalds check of P L U Q = A failed"
 
 
-@pytest.mark.parametrize("form", ["auto", "fp64"])
+@pytest.mark.parametrize("form", ["limb", "fp64"])
 def test_config_lru_8192(ctx, form):
     cfg = workloads.CONFIGS["lru-8192-r4096-p131071"]
     g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
