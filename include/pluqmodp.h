@@ -142,9 +142,29 @@ int pluq_last_rank(pluq_ctx* ctx, int64_t* rank);
  * value. */
 int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 
+/* Largest block (rows and columns, 0..2048) factored as one leaf by a
+ * cooperative grid over all SMs (pivot search and elimination with one grid
+ * barrier per pivot); 0 disables leaves so the recursion descends to
+ * one-CTA base-case tiles.  Default 2048. */
+int pluq_set_leaf(pluq_ctx* ctx, int leaf_dim);
+
 /* Counters of the last call: base-case launches, internal recursion nodes,
  * fgemm calls. */
 int pluq_last_stats(pluq_ctx* ctx, int64_t* n_base, int64_t* n_nodes, int64_t* n_gemm);
+
+/* Per-kernel-class timers.  pluq_profile_enable(ctx, 1) resets the counters
+ * and brackets every later kernel launch with CUDA events on the call's
+ * stream (0 stops recording; launches are counted either way).
+ * pluq_profile_read(ctx, cls, ...) waits for the recorded events and returns,
+ * for class cls (0 base-case tile, 1 fgemm tensor kernel, 2 operand packing,
+ * 3 triangular diagonal blocks, 4 block gathers, 5 index vectors, 6 other),
+ * the launch count, the summed device time in ms, the summed algorithmic
+ * field operations (2 M N K for an fgemm) and bytes, and the summed tensor-pipe
+ * flops actually issued (digit products included) of the timed launches.
+ * Any output pointer may be NULL. */
+int pluq_profile_enable(pluq_ctx* ctx, int enable);
+int pluq_profile_read(pluq_ctx* ctx, int cls, int64_t* launches, double* ms, double* flops,
+                      double* bytes, double* tensor_flops);
 
 /* Human-readable name of a status code (static string). */
 const char* pluq_status_string(int status);

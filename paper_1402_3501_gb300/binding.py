@@ -33,7 +33,7 @@ _lib = None
 SYMBOLS = [
     "pluq_create", "pluq_destroy", "pluq_modp", "echelon_modp", "rank_profile_modp",
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
-    "pluq_status_string",
+    "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
 ]
 
 
@@ -65,6 +65,9 @@ def load():
         "pluq_set_tuning": [vp, i32, i32, i32],
         "pluq_last_stats": [vp, vp, vp, vp],
         "pluq_status_string": [i32],
+        "pluq_profile_enable": [vp, i32],
+        "pluq_set_leaf": [vp, i32],
+        "pluq_profile_read": [vp, i32, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -131,8 +134,31 @@ class Context:
         except Exception:
             pass
 
+    def set_leaf(self, leaf_dim: int):
+        """Largest block factored by one cooperative leaf launch (0: one-CTA tiles only)."""
+        _check(load().pluq_set_leaf(self.handle, leaf_dim), "pluq_set_leaf")
+
     def set_tuning(self, bm: int = 0, bn: int = 0, trsm_block: int = 0):
         _check(load().pluq_set_tuning(self.handle, bm, bn, trsm_block), "pluq_set_tuning")
+
+    PROFILE_CLASSES = ["base", "fgemm", "pack", "trsm", "perm", "index", "other"]
+
+    def profile(self, enable: bool = True):
+        """Reset the per-class launch counters; with enable, time every launch."""
+        _check(load().pluq_profile_enable(self.handle, 1 if enable else 0), "pluq_profile_enable")
+
+    def profile_read(self) -> dict:
+        """Per kernel class: launches, device ms, algorithmic flops/bytes, tensor flops."""
+        out = {}
+        for k, name in enumerate(self.PROFILE_CLASSES):
+            nl, ms, fl, by, tf = (ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(),
+                                  ctypes.c_double(), ctypes.c_double())
+            _check(load().pluq_profile_read(self.handle, k, ctypes.byref(nl), ctypes.byref(ms),
+                                            ctypes.byref(fl), ctypes.byref(by), ctypes.byref(tf)),
+                   "pluq_profile_read")
+            out[name] = {"launches": nl.value, "ms": ms.value, "flops": fl.value,
+                         "bytes": by.value, "tensor_flops": tf.value}
+        return out
 
     def last_stats(self) -> dict:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

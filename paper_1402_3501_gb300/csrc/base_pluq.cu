@@ -183,6 +183,7 @@ int launch_base_pluq(pluq_ctx* c, uint32_t* A, int64_t lda, int m, int n, int32_
     attr_set = true;
   }
   if (m > kBM || n > kBN || m <= 0 || n <= 0) return PLUQ_ERR_INVALID_ARG;
+  ProfScope ps(c, PC_BASE, 0, 8.0 * m * n);
   k_base_pluq<<<1, kBaseThreads, kBaseSmem, c->stream>>>(A, lda, m, n, c->F, inv_table_ptr(c),
                                                         perm_r, perm_c, rank_out);
   PLUQ_CUDA(cudaGetLastError());
@@ -197,6 +198,7 @@ int ensure_inv_table(pluq_ctx* c) {
   if (p >= kInvTableMaxP || p == 2) return PLUQ_OK;
   if (c->inv_table_p == p) return PLUQ_OK;
   PLUQ_TRY(c->inv_table.ensure(sizeof(uint32_t) * p));
+  ProfScope ps(c, PC_OTHER, 0, 4.0 * p);
   k_inv_table<<<(unsigned)cdiv(p, 256), 256, 0, c->stream>>>(c->inv_table.as<uint32_t>(), p);
   PLUQ_CUDA(cudaGetLastError());
   c->inv_table_p = p;

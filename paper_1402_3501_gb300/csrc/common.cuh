@@ -53,7 +53,34 @@ struct DevBuf {
 // halves at least one dimension, and dimensions are < 2^31).
 constexpr int kMaxDepth = 72;
 
+// Kernel classes for the per-class CUDA-event timers.
+enum ProfClass {
+  PC_BASE = 0,  // base-case PLUQ tile
+  PC_FGEMM,     // fgemm tensor kernel (limb tcgen05 or FP64 DMMA)
+  PC_PACK,      // digit-plane packing of fgemm operands
+  PC_TRSM,      // diagonal-block triangular solves
+  PC_PERM,      // row / column block gathers and copy-back
+  PC_INDEX,     // index-vector kernels (iota, compose, shifts)
+  PC_OTHER,     // range check, copies, profiles, RREF scatter
+  PC_COUNT
+};
+
+struct ProfRec {
+  int cls;
+  int a, b;  // indices into the event pool
+  double flops, bytes, tflops;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<ProfRec> recs;
+};
+
 struct pluq_ctx {
+  Profiler prof;
+  int64_t launches[PC_COUNT] = {0, 0, 0, 0, 0, 0, 0};
   int device = 0;
   int sm_count = 0;
   cudaStream_t stream = nullptr;
@@ -61,6 +88,7 @@ struct pluq_ctx {
   int form = PLUQ_FORM_FP64;
   int bm = 128, bn = 128;  // base-case tile
   int trsm_block = 64;     // diagonal block of the triangular solves
+  int leaf_dim = 2048;     // cooperative leaves up to leaf_dim x leaf_dim (0: off)
   int64_t mmax = 0, nmax = 0;
   // workspace
   DevBuf scratch;          // uint32 gathers, packed GEMM operands
@@ -71,15 +99,30 @@ struct pluq_ctx {
   DevBuf inv_table;        // uint32[p] inverses when p is small
   uint32_t inv_table_p = 0;
   DevBuf work;             // a copy of A for echelon / rank-profile calls
+  DevBuf leaf;             // grid-barrier words and candidate rows of leaf launches
   int32_t* host_small = nullptr;  // pinned host scalars
   // per-call statistics (host side)
   int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
   // device error flag (int) lives in small at offset 0
 };
 
+// Count a kernel launch of class `cls` and, when profiling, bracket it with a
+// pair of CUDA events on the context stream (work = algorithmic flops/bytes).
+struct ProfScope {
+  pluq_ctx* c;
+  int idx = -1;
+  ProfScope(pluq_ctx* ctx, int cls, double flops = 0, double bytes = 0, int nlaunch = 1,
+            double tflops = 0);
+  ~ProfScope();
+};
+
 // kernels / helpers implemented in the .cu files
 int launch_base_pluq(pluq_ctx* c, uint32_t* A, int64_t lda, int m, int n, int32_t* perm_r,
                      int32_t* perm_c, int32_t* rank_out);
+int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
+                     int32_t* perm_c, int32_t* rank_out);
+int leaf_fits(pluq_ctx* c, int64_t m, int64_t n);
+int leaf_max_dim();
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
 int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t count);
 int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const int64_t* seg_len,

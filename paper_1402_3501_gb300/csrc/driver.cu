@@ -212,9 +212,13 @@ struct Recursion {
       PLUQ_TRY(launch_iota(c, pc, n));
       return PLUQ_OK;
     }
-    if (m <= c->bm && n <= c->bn) {
+    const bool leaf = c->leaf_dim > 0 && leaf_fits(c, m, n);
+    if (leaf || (m <= c->bm && n <= c->bn)) {
       c->n_base++;
-      PLUQ_TRY(launch_base_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      if (leaf)
+        PLUQ_TRY(launch_leaf_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      else
+        PLUQ_TRY(launch_base_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
       // rank (int 8 of the scalar block) and the device error word (int 16)
       PLUQ_CUDA(cudaMemcpyAsync(c->host_small, c->small.ptr, 32 * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, c->stream));
@@ -225,8 +229,10 @@ struct Recursion {
     }
     if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
     c->n_nodes++;
-    const int64_t m1 = m > c->bm ? split(m) : m;
-    const int64_t n1 = n > c->bn ? split(n) : n;
+    const int64_t lim_m = c->leaf_dim > 0 ? c->leaf_dim : c->bm;
+    const int64_t lim_n = c->leaf_dim > 0 ? c->leaf_dim : c->bn;
+    const int64_t m1 = m > lim_m ? split(m) : m;
+    const int64_t n1 = n > lim_n ? split(n) : n;
     const int64_t m2 = m - m1, n2 = n - n1;
     int32_t* cr = PR(d + 1);
     int32_t* cc = PC(d + 1);
@@ -358,6 +364,7 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
   int* flag = c->small.as<int>();
   PLUQ_CUDA(cudaMemsetAsync(flag, 0, 256, c->stream));
   if (m > 0 && n > 0) {
+    ProfScope ps(c, PC_OTHER, 0, 4.0 * m * n);
     k_check_range<<<grid2(m, n), 256, 0, c->stream>>>(A, lda, m, n, c->F.p, flag);
     PLUQ_CUDA(cudaGetLastError());
     PLUQ_CUDA(cudaMemcpyAsync(c->host_small, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -383,14 +390,17 @@ int write_outputs(pluq_ctx* c, int64_t m, int64_t n, int64_t r, int32_t* P, int3
   if (Q && n > 0)
     PLUQ_CUDA(cudaMemcpyAsync(Q, PC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
   if (rank_dev) {
+    ProfScope ps(c, PC_OTHER);
     k_store_rank<<<1, 1, 0, c->stream>>>(rank_dev, r);
     PLUQ_CUDA(cudaGetLastError());
   }
   if (rrp && r > 0) {
+    ProfScope ps(c, PC_OTHER, 0, 4.0 * r);
     k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(m, 32), c->stream>>>(PR, r, m, rrp);
     PLUQ_CUDA(cudaGetLastError());
   }
   if (crp && r > 0) {
+    ProfScope ps(c, PC_OTHER, 0, 4.0 * r);
     k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(n, 32), c->stream>>>(PC, r, n, crp);
     PLUQ_CUDA(cudaGetLastError());
   }
@@ -400,6 +410,7 @@ int write_outputs(pluq_ctx* c, int64_t m, int64_t n, int64_t r, int32_t* P, int3
 int copy_to_work(pluq_ctx* c, int64_t m, int64_t n, const uint32_t* A, int64_t lda) {
   PLUQ_TRY(c->work.ensure(sizeof(uint32_t) * std::max<int64_t>(m * n, 1)));
   if (m > 0 && n > 0) {
+    ProfScope ps(c, PC_OTHER, 0, 8.0 * m * n);
     k_copy_mat<<<grid2(m, n), 256, 0, c->stream>>>(c->work.as<uint32_t>(), n, A, lda, m, n);
     PLUQ_CUDA(cudaGetLastError());
   }
@@ -407,6 +418,31 @@ int copy_to_work(pluq_ctx* c, int64_t m, int64_t n, const uint32_t* A, int64_t l
 }
 
 }  // namespace
+
+ProfScope::ProfScope(pluq_ctx* ctx, int cls, double flops, double bytes, int nlaunch,
+                     double tflops)
+    : c(ctx) {
+  c->launches[cls] += nlaunch;
+  if (!c->prof.on) return;
+  Profiler& P = c->prof;
+  while (P.used + 2 > P.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    P.pool.push_back(e);
+  }
+  ProfRec r{cls, (int)P.used, (int)P.used + 1, flops, bytes, tflops};
+  P.used += 2;
+  cudaEventRecord(P.pool[r.a], c->stream);
+  P.recs.push_back(r);
+  idx = (int)P.recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx >= 0) cudaEventRecord(c->prof.pool[c->prof.recs[idx].b], c->stream);
+}
 
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
@@ -447,8 +483,10 @@ int pluq_destroy(pluq_ctx* c) {
   c->perm_r.release();
   c->perm_c.release();
   c->tmp_i.release();
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   c->small.release();
   c->inv_table.release();
+  c->leaf.release();
   c->work.release();
   if (c->host_small) cudaFreeHost(c->host_small);
   delete c;
@@ -479,6 +517,7 @@ int rank_profile_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint3
   if (rpm_col_of_row && m > 0) {
     const int32_t* PR = c->perm_r.as<int32_t>();
     const int32_t* PC = c->perm_c.as<int32_t>();
+    ProfScope ps(c, PC_OTHER, 0, 4.0 * m, r > 0 ? 2 : 1);
     k_rpm_col_of_row<<<(unsigned)cdiv(m, 256), 256, 0, c->stream>>>(PR, PC, r, m, rpm_col_of_row);
     if (r > 0) k_rpm_fill<<<(unsigned)cdiv(r, 256), 256, 0, c->stream>>>(PR, PC, r, rpm_col_of_row);
     PLUQ_CUDA(cudaGetLastError());
@@ -506,6 +545,7 @@ int echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* 
   int32_t* qinv = ints;
   int32_t* crp_buf = crp ? crp : ints + n;
   const int32_t* PC = c->perm_c.as<int32_t>();
+  ProfScope ps(c, PC_OTHER, 0, 8.0 * n + 4.0 * r * n, 3);
   k_invert_perm<<<(unsigned)cdiv(n, 256), 256, 0, c->stream>>>(PC, n, qinv);
   k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(n, 32), c->stream>>>(PC, r, n, crp_buf);
   k_rref_scatter<<<grid2(r, n), 256, 0, c->stream>>>(W, ldw, r, n, qinv, crp_buf, R, ldr);
@@ -557,11 +597,50 @@ int pluq_set_tuning(pluq_ctx* c, int bm, int bn, int trsm_block) {
   return PLUQ_OK;
 }
 
+int pluq_set_leaf(pluq_ctx* c, int leaf_dim) {
+  if (!c || leaf_dim < 0 || leaf_dim > leaf_max_dim()) return PLUQ_ERR_INVALID_ARG;
+  c->leaf_dim = leaf_dim;
+  return PLUQ_OK;
+}
+
 int pluq_last_stats(pluq_ctx* c, int64_t* n_base, int64_t* n_nodes, int64_t* n_gemm) {
   if (!c) return PLUQ_ERR_INVALID_ARG;
   if (n_base) *n_base = c->n_base;
   if (n_nodes) *n_nodes = c->n_nodes;
   if (n_gemm) *n_gemm = c->n_gemm;
+  return PLUQ_OK;
+}
+
+int pluq_profile_enable(pluq_ctx* c, int enable) {
+  if (!c) return PLUQ_ERR_INVALID_ARG;
+  c->prof.on = enable != 0;
+  c->prof.used = 0;
+  c->prof.recs.clear();
+  for (int k = 0; k < PC_COUNT; ++k) c->launches[k] = 0;
+  return PLUQ_OK;
+}
+
+int pluq_profile_read(pluq_ctx* c, int cls, int64_t* launches, double* ms, double* flops,
+                      double* bytes, double* tensor_flops) {
+  if (!c || cls < 0 || cls >= PC_COUNT) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_CUDA(cudaSetDevice(c->device));
+  int64_t nl = c->launches[cls];
+  double t = 0, f = 0, b = 0, tf = 0;
+  for (const ProfRec& r : c->prof.recs) {
+    if (r.cls != cls) continue;
+    float e = 0;
+    PLUQ_CUDA(cudaEventSynchronize(c->prof.pool[r.b]));
+    PLUQ_CUDA(cudaEventElapsedTime(&e, c->prof.pool[r.a], c->prof.pool[r.b]));
+    t += e;
+    f += r.flops;
+    b += r.bytes;
+    tf += r.tflops;
+  }
+  if (launches) *launches = nl;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  if (bytes) *bytes = b;
+  if (tensor_flops) *tensor_flops = tf;
   return PLUQ_OK;
 }
 

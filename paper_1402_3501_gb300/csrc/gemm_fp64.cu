@@ -118,6 +118,8 @@ int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
   const int per_reduce = kt >= total_kt ? 0 : (int)kt;
   const dim3 grid((unsigned)cdiv(N, kBNf), (unsigned)cdiv(M, kBMf), 1);
   if (grid.y > 65535) return PLUQ_ERR_INVALID_ARG;
+  ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K, 4.0 * (M * K + K * N + 2 * M * N), 1,
+               2.0 * cdiv(M, kBMf) * kBMf * cdiv(N, kBNf) * kBNf * cdiv(K, kBKf) * kBKf);
   k_fgemm_fp64<<<grid, kThreadsF, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->F.p,
                                                   (double)c->F.p, 1.0 / (double)c->F.p,
                                                   per_reduce);

@@ -519,6 +519,7 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   __half* Ap = c->pack.as<__half>();
   __half* Bp = reinterpret_cast<__half*>(reinterpret_cast<char*>(Ap) + ((abytes + 1023) / 1024) * 1024);
   {
+    ProfScope ps(c, PC_PACK, 0, 4.0 * (M * K + K * N) + (double)abytes + (double)bbytes, 2);
     dim3 g((unsigned)std::min<int64_t>(cdiv(Kp, 256), 64), (unsigned)std::min<int64_t>(Mp, 65535));
     k_pack_rows<L><<<g, 256, 0, c->stream>>>(A, lda, M, K, Mp, Kp, c->F.p, Ap);
     dim3 g2((unsigned)cdiv(Kp, 32), (unsigned)cdiv(Np, 32));
@@ -531,6 +532,9 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   const dim3 grid((unsigned)(Np / kTN), (unsigned)(Mp / kTM));
   if (grid.y > 65535 || cdiv(Np, 32) > 65535) return PLUQ_ERR_INVALID_ARG;
   int* err = c->small.as<int>() + 16;
+  ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K,
+               (double)abytes + (double)bbytes + 8.0 * M * N, 1,
+               2.0 * Mp * Np * Kp * L * L);
   k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, c->stream>>>(
       ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK), pl.group_kb, C, ldc, c->F, pl.bias, err);
   PLUQ_CUDA(cudaGetLastError());

@@ -105,6 +105,7 @@ dim3 grid2d(int64_t rows, int64_t cols, int threads) {
 
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count) {
   if (count <= 0) return PLUQ_OK;
+  ProfScope ps(c, PC_INDEX, 0, 4.0 * count);
   k_iota<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(dst, count);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
@@ -112,6 +113,7 @@ int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count) {
 
 int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t count) {
   if (count <= 1) return PLUQ_OK;
+  ProfScope ps(c, PC_INDEX, 0, 12.0 * count, count <= 12288 ? 1 : 2);
   if (count <= 12288) {
     k_compose_smem<<<1, 1024, sizeof(int32_t) * count, c->stream>>>(base, perm, (int)count);
   } else {
@@ -135,6 +137,7 @@ int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const in
     total += seg_len[k];
   }
   if (total <= 0) return PLUQ_OK;
+  ProfScope ps(c, PC_INDEX, 0, 4.0 * total);
   k_segperm<<<(unsigned)cdiv(total, 256), 256, 0, c->stream>>>(out, sg, total);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
@@ -146,6 +149,7 @@ int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t co
   PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
   uint32_t* S = c->scratch.as<uint32_t>();
   const dim3 g = grid2d(rows, cols, 256);
+  ProfScope ps(c, PC_PERM, 0, 8.0 * rows * cols, 2);
   k_gather_rows<<<g, 256, 0, c->stream>>>(S, cols, A, lda, rows, cols, perm);
   k_copy2d<<<g, 256, 0, c->stream>>>(A, lda, S, cols, rows, cols);
   PLUQ_CUDA(cudaGetLastError());
@@ -158,6 +162,7 @@ int permute_cols(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t co
   PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
   uint32_t* S = c->scratch.as<uint32_t>();
   const dim3 g = grid2d(rows, cols, 256);
+  ProfScope ps(c, PC_PERM, 0, 8.0 * rows * cols, 2);
   k_gather_cols<<<g, 256, 0, c->stream>>>(S, cols, A, lda, rows, cols, perm);
   k_copy2d<<<g, 256, 0, c->stream>>>(A, lda, S, cols, rows, cols);
   PLUQ_CUDA(cudaGetLastError());

@@ -124,6 +124,7 @@ int trsm_left_lower_unit(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r,
   if (r <= 1 || ncols <= 0) return PLUQ_OK;  // a unit 1x1 triangle is the identity
   const int64_t tb = c->trsm_block < kTB ? c->trsm_block : kTB;
   if (r <= tb) {
+    ProfScope ps(c, PC_TRSM, (double)r * r * ncols, 8.0 * r * ncols);
     k_trsm_llu_small<<<(unsigned)cdiv(ncols, kStrip), kTrsmThreads, 0, c->stream>>>(
         L, ldl, (int)r, B, ldb, ncols, c->F);
     PLUQ_CUDA(cudaGetLastError());
@@ -140,6 +141,7 @@ int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uin
   if (r <= 0 || nrows <= 0) return PLUQ_OK;
   const int64_t tb = c->trsm_block < kTB ? c->trsm_block : kTB;
   if (r <= tb) {
+    ProfScope ps(c, PC_TRSM, (double)r * r * nrows, 8.0 * r * nrows);
     k_trsm_ru_small<<<(unsigned)cdiv(nrows, kStrip), kTrsmThreads, 0, c->stream>>>(
         U, ldu, (int)r, B, ldb, nrows, c->F, inv_table_ptr(c));
     PLUQ_CUDA(cudaGetLastError());
@@ -156,6 +158,7 @@ int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint
   if (r <= 0 || ncols <= 0) return PLUQ_OK;
   const int64_t tb = c->trsm_block < kTB ? c->trsm_block : kTB;
   if (r <= tb) {
+    ProfScope ps(c, PC_TRSM, (double)r * r * ncols, 8.0 * r * ncols);
     k_trsm_lu_small<<<(unsigned)cdiv(ncols, kStrip), kTrsmThreads, 0, c->stream>>>(
         U, ldu, (int)r, B, ldb, ncols, c->F, inv_table_ptr(c));
     PLUQ_CUDA(cudaGetLastError());

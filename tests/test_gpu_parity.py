@@ -31,6 +31,21 @@ def ctx():
     c.close()
 
 
+class leaf_mode:
+    """Temporarily set the leaf size (0: one-CTA tiles) and base tiles."""
+
+    def __init__(self, ctx, leaf, tiles=(128, 128), trsm_block=64):
+        self.ctx, self.leaf, self.tiles, self.tb = ctx, leaf, tiles, trsm_block
+
+    def __enter__(self):
+        self.ctx.set_leaf(self.leaf)
+        self.ctx.set_tuning(self.tiles[0], self.tiles[1], self.tb)
+
+    def __exit__(self, *exc):
+        self.ctx.set_leaf(2048)
+        self.ctx.set_tuning(128, 128, 64)
+
+
 def to_dev(A):
     return torch.from_numpy(np.ascontiguousarray(A).astype(np.int32)).cuda()
 
@@ -116,51 +131,50 @@ SHAPES = [(1, 1), (1, 40), (40, 1), (17, 33), (128, 128), (129, 130), (200, 300)
           (513, 257)]
 
 
+@pytest.mark.parametrize("leaf", [2048, 0])
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("p", [2, 3, 65521, 131071])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_pluq_uniform(ctx, form, p, shape):
+def test_pluq_uniform(ctx, leaf, form, p, shape):
     m, n = shape
     A = workloads.uniform_matrix(m, n, p, seed=1)
-    assert_parity(ctx, A, p, form)
+    with leaf_mode(ctx, leaf):
+        assert_parity(ctx, A, p, form)
 
 
+@pytest.mark.parametrize("leaf", [2048, 96, 0])
 @pytest.mark.parametrize("p", [3, 131071])
 @pytest.mark.parametrize("shape", [(64, 64), (150, 200), (300, 260), (513, 257), (700, 700)])
 @pytest.mark.parametrize("frac", [0.0, 0.1, 0.5, 0.9])
-def test_pluq_prescribed_rank(ctx, p, shape, frac):
+def test_pluq_prescribed_rank(ctx, leaf, p, shape, frac):
     m, n = shape
     r = int(min(m, n) * frac)
     g = workloads.prescribed_rank_matrix(m, n, r, p, seed=2)
-    got = assert_parity(ctx, g.A, p)
+    with leaf_mode(ctx, leaf):
+        got = assert_parity(ctx, g.A, p)
     assert got == r
 
 
-@pytest.mark.parametrize("tiles", [(8, 8), (16, 8), (5, 13), (32, 32), (128, 64)])
+@pytest.mark.parametrize("mode", [(0, (8, 8)), (0, (16, 8)), (0, (5, 13)), (0, (32, 32)),
+                                  (0, (128, 64)), (9, (8, 8)), (24, (8, 8)), (40, (8, 8))])
 @pytest.mark.parametrize("seed", [1, 2])
-def test_pluq_deep_recursion(ctx, tiles, seed):
-    # small base tiles drive many recursion levels through every block step
+def test_pluq_deep_recursion(ctx, mode, seed):
+    # small leaves / base tiles drive many recursion levels through every block step
     p = 131071
-    ctx.set_tuning(tiles[0], tiles[1], 0)
-    try:
+    with leaf_mode(ctx, mode[0], mode[1]):
         for m, n, frac in [(90, 70, 0.5), (64, 100, 0.3), (133, 133, 1.0)]:
             g = workloads.prescribed_rank_matrix(m, n, int(min(m, n) * frac), p, seed)
             assert_parity(ctx, g.A, p)
         A = workloads.uniform_matrix(77, 91, 5, seed)
         assert_parity(ctx, A, 5)
-    finally:
-        ctx.set_tuning(128, 128, 0)
 
 
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
 def test_pluq_trsm_blocks(ctx, tb):
     p = 65521
-    ctx.set_tuning(32, 32, tb)
-    try:
+    with leaf_mode(ctx, 40, (32, 32), tb):
         g = workloads.prescribed_rank_matrix(260, 240, 180, p, seed=4)
         assert_parity(ctx, g.A, p)
-    finally:
-        ctx.set_tuning(128, 128, 64)
 
 
 def test_pluq_special_matrices(ctx):
