@@ -168,10 +168,17 @@ def bench_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    cfg = workloads.CONFIGS[WORKLOAD]
-    m, n, r, p = cfg.m, cfg.n, cfg.r, cfg.p
-    g = workloads.prescribed_rank_matrix(m, n, r, p, seed=1, device="cuda")
-    A0 = torch.from_numpy(g.A.astype(np.int32)).cuda()
+    cfg = workloads.CONFIGS[args.workload]
+    m, n, p = cfg.m, cfg.n, cfg.p
+    if cfg.kind == "uniform":
+        # profiling case only: full rank with high probability, no construction to
+        # check against here (the parity tests compare it with the oracle)
+        g = None
+        A_host = workloads.uniform_matrix(m, n, p, seed=1)
+    else:
+        g = workloads.prescribed_rank_matrix(m, n, cfg.r, p, seed=1, device="cuda")
+        A_host = g.A
+    A0 = torch.from_numpy(A_host.astype(np.int32)).cuda()
     A = torch.empty_like(A0)
     ctx = pq.Context(local)
     stream = torch.cuda.current_stream()
@@ -182,11 +189,14 @@ def bench_ours(args, world, rank, local):
         A.copy_(A0)
         res = pq.pluq_modp(A, p, form=form, ctx=ctx)
     torch.cuda.synchronize()
-    P = res.P.cpu().numpy()
-    Q = res.Q.cpu().numpy()
-    exact = (res.rank == r and set(zip(P[:r].tolist(), Q[:r].tolist())) == g.rpm
-             and res.rrp.cpu().tolist() == g.rrp.tolist()
-             and res.crp.cpu().tolist() == g.crp.tolist())
+    r = res.rank
+    exact = None
+    if g is not None:
+        P = res.P.cpu().numpy()
+        Q = res.Q.cpu().numpy()
+        exact = (r == g.rank and set(zip(P[:r].tolist(), Q[:r].tolist())) == g.rpm
+                 and res.rrp.cpu().tolist() == g.rrp.tolist()
+                 and res.crp.cpu().tolist() == g.crp.tolist())
 
     # timed region: CUDA events on the launching stream around K steps; the
     # library counts its own kernel launches
@@ -226,7 +236,7 @@ def bench_ours(args, world, rank, local):
 
     # end to end through the public API: pinned host input -> device -> PLUQ ->
     # L\U, P, Q back to pinned host memory
-    Ah = torch.from_numpy(g.A.astype(np.int32)).pin_memory()
+    Ah = torch.from_numpy(A_host.astype(np.int32)).pin_memory()
     LUh = torch.empty_like(Ah).pin_memory()
     Ph = torch.empty(m, dtype=torch.int32).pin_memory()
     Qh = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -274,7 +284,7 @@ def bench_ours(args, world, rank, local):
         import oracle
         cores = os.cpu_count() or 1
         t = time.time()
-        ref = oracle.pluq(g.A, p, threads=cores)
+        ref = oracle.pluq(A_host, p, threads=cores)
         dt = time.time() - t
         assert ref.rank == r
         cpu = {"value": round(F / dt / 1e9, 3), "unit": "Gfops", "cores": cores, "kind": "oracle",
@@ -286,11 +296,11 @@ def bench_ours(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r, "p": p, "form": form,
+            "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "p": p, "form": form,
                        "l2": "inputs (268 MB) larger than L2 (129 MB), no flush",
                        "step": "restore input (D2D copy) + pluq_modp",
                        "parallelism": f"replicas x{world}"},
-            "bitexact": bool(exact),
+            "bitexact": exact,
             "fgemm_dtype": "f16 digits, f32 accumulate" if form != "fp64" else "f64",
             "fp64_form": fp64,
             "e2e": {"value": round(world * F / (e2e_ms / 1e3) / 1e9, 3), "unit": "Gfops",
@@ -319,6 +329,10 @@ def main():
     ap.add_argument("--form", choices=["limb", "fp64", "auto"], default="limb")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[k for k, v in workloads.CONFIGS.items() if v.kind != "batched"],
+                    help="matrix to factor (the default is the measured workload; the "
+                         "others serve as small profiling cases)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()

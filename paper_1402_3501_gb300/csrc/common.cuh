@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "../../include/pluqmodp.h"
+#include "pluqmodp.h"
 #include "field.cuh"
 
 #define PLUQ_CUDA(call)                                   \

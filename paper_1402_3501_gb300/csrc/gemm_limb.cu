@@ -316,17 +316,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         if (!last_group) {
           tmem_st16(lane_base + Cfg::kResCol + col, res);
-        } else if (grow < M) {
-          uint32_t* crow = C + grow * ldc;
+        } else {
+          // residue holds (sum t) R^{-1}; one more step with R^2 undoes it.
+          // Stage the tile in the (now idle) pipeline shared memory so that
+          // C is updated with row-contiguous accesses below.
+          uint32_t* stage = reinterpret_cast<uint32_t*>(smem) + row * (kTN + 1) + col;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int64_t gc = (int64_t)n0 + col + e;
-            if (gc < N) {
-              // residue holds (sum t) R^{-1}; one more step with R^2 undoes it
-              const uint32_t fin = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
-              crow[gc] = f_sub(crow[gc], fin, F);
-            }
-          }
+          for (int e = 0; e < 16; ++e)
+            stage[e] = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
         }
       }
       if (!last_group) {
@@ -334,6 +331,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
+      }
+    }
+    // C <- C - residue, one warp per row, 32 consecutive columns per access
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (*(volatile int*)abort_flag == 0) {
+      const int ew = warp - 2;
+      const uint32_t* stage = reinterpret_cast<const uint32_t*>(smem);
+      for (int rr = ew; rr < kTM; rr += 8) {
+        const int64_t gr = (int64_t)m0 + rr;
+        if (gr >= M) break;
+        uint32_t* crow = C + gr * ldc + n0;
+        uint32_t cv[kTN / 32];
+#pragma unroll
+        for (int q2 = 0; q2 < kTN / 32; ++q2) {
+          const int j = lane + 32 * q2;
+          cv[q2] = (n0 + j < N) ? crow[j] : 0u;
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < kTN / 32; ++q2) {
+          const int j = lane + 32 * q2;
+          if (n0 + j < N) crow[j] = f_sub(cv[q2], stage[rr * (kTN + 1) + j], F);
+        }
       }
     }
   }
