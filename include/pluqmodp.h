@@ -48,6 +48,7 @@ extern "C" {
 #define PLUQ_ERR_NO_WORKSPACE -6       /* device workspace allocation failed */
 #define PLUQ_ERR_CUDA -7               /* a CUDA runtime call failed */
 #define PLUQ_ERR_TIMEOUT -8            /* a bounded device wait ran out */
+#define PLUQ_ERR_TOO_LARGE -9          /* exceeds the fixed scratch of fgemm_modp_noalloc */
 
 /* fgemm forms for the Schur-complement updates (Sec. 3.1).
  *   FP64:     residues embedded in doubles, products on FP64 DMMA tensor
@@ -121,6 +122,26 @@ int rank_profile_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uin
 int fgemm_modp(pluq_ctx* ctx, uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
                int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc, int form,
                void* stream);
+
+/* fgemm_modp for callers that cannot allocate device memory (no cudaMalloc,
+ * cudaFree or allocating library call happens inside).  The paper has no
+ * counterpart: this is a deployment variant of the limb form of fgemm_modp.
+ *   Computes C <- C - A B mod p exactly, as fgemm_modp with
+ *   PLUQ_FORM_LIMB_F16; same argument layout, no context.  The digit planes
+ *   live in one 32 MiB device array inside the library that each GPU loading
+ *   the library keeps until process exit; problems whose planes exceed it,
+ *   2 L (ceil(M/128)*128 + ceil(N/128)*128) ceil(K/64)*64 bytes with L = 2
+ *   digits for p up to about 2^18 (1 for p below 512), return
+ *   PLUQ_ERR_TOO_LARGE.
+ *   The first call on a device looks up that array's device address (with
+ *   the device current), so make it before any stream capture.  All calls
+ *   share the array: calls that overlap on the GPU (other streams, other
+ *   host threads) race; issue them on one stream.
+ * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM (p has no limb plan), TOO_LARGE,
+ * CUDA. */
+int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+                       int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc,
+                       void* stream);
 
 /* Batched PLUQ of `batch` independent matrices (each as pluq_modp).
  *   m, n, lda   host int64 arrays of length batch.

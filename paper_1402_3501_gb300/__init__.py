@@ -7,11 +7,11 @@ holds the CUDA sources (csrc/), the in-tree build (build.py) and the Python
 binding (binding.py).
 """
 from .binding import (FORM_AUTO, FORM_FP64, FORM_LIMB_F16, Context, PluqError, PLUQResult,
-                      default_context, echelon_modp, fgemm_modp, load, pluq_modp,
+                      default_context, echelon_modp, fgemm_modp, fgemm_modp_noalloc, load, pluq_modp,
                       pluq_modp_batched, rank_profile_modp)
 
 __all__ = [
     "FORM_AUTO", "FORM_FP64", "FORM_LIMB_F16", "Context", "PluqError", "PLUQResult",
-    "default_context", "echelon_modp", "fgemm_modp", "load", "pluq_modp", "pluq_modp_batched",
+    "default_context", "echelon_modp", "fgemm_modp", "fgemm_modp_noalloc", "load", "pluq_modp", "pluq_modp_batched",
     "rank_profile_modp",
 ]

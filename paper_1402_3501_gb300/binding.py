@@ -25,6 +25,7 @@ STATUS = {
     0: "ok", -1: "invalid argument", -2: "p is not prime", -3: "p out of range",
     -4: "matrix entry >= p", -5: "fgemm form unsupported for this p",
     -6: "device workspace allocation failed", -7: "CUDA error", -8: "device wait timed out",
+    -9: "exceeds the fixed scratch of the non-allocating entry point",
 }
 
 _lib = None
@@ -34,6 +35,7 @@ SYMBOLS = [
     "pluq_create", "pluq_destroy", "pluq_modp", "echelon_modp", "rank_profile_modp",
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
     "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
+    "fgemm_modp_noalloc",
 ]
 
 
@@ -67,6 +69,7 @@ def load():
         "pluq_status_string": [i32],
         "pluq_profile_enable": [vp, i32],
         "pluq_set_leaf": [vp, i32],
+        "fgemm_modp_noalloc": [u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp],
         "pluq_profile_read": [vp, i32, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -253,6 +256,25 @@ def fgemm_modp(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, p: int, form="
     st = load().fgemm_modp(ctx.handle, p, M, N, K, _dev_ptr(A), lda, _dev_ptr(B), ldb,
                            _dev_ptr(C), ldc, _form(form), _stream_handle(stream))
     _check(st, "fgemm_modp")
+    return C
+
+
+def fgemm_modp_noalloc(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, p: int,
+                       stream=None) -> torch.Tensor:
+    """C <- C - A B mod p through the entry point that allocates no device memory.
+
+    For callers that cannot allocate (the library uses a fixed 32 MiB device
+    array instead of context workspace); concurrent calls on different
+    streams race on that array.
+    """
+    M, K, lda = _matrix_args(A, "A")
+    K2, N, ldb = _matrix_args(B, "B")
+    M2, N2, ldc = _matrix_args(C, "C")
+    if K2 != K or M2 != M or N2 != N:
+        raise ValueError("shape mismatch")
+    st = load().fgemm_modp_noalloc(p, M, N, K, _dev_ptr(A), lda, _dev_ptr(B), ldb, _dev_ptr(C),
+                                   ldc, _stream_handle(stream))
+    _check(st, "fgemm_modp_noalloc")
     return C
 
 

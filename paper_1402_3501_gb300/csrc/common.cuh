@@ -145,6 +145,8 @@ int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
 int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,
                    int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
 int limb_form_supported(uint32_t p);
+// PLUQ_OK when p is a prime in [2, 2^31), else P_OUT_OF_RANGE / P_NOT_PRIME.
+int check_prime_range(uint32_t p);
 int fp64_form_supported(uint32_t p);
 int ensure_inv_table(pluq_ctx* c);
 const uint32_t* inv_table_ptr(pluq_ctx* c);

@@ -444,6 +444,8 @@ ProfScope::~ProfScope() {
   if (idx >= 0) cudaEventRecord(c->prof.pool[c->prof.recs[idx].b], c->stream);
 }
 
+int check_prime_range(uint32_t p) { return check_p(p); }
+
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -576,4 +577,111 @@ int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
   if (cached.L == 1) return run_limb<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   if (cached.L == 2) return run_limb<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   return PLUQ_ERR_UNSUPPORTED_FORM;
+}
+
+// ---------------------------------------------------------------------------
+// fgemm_modp_noalloc: the limb fgemm without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code running while another component
+// owns the device memory through its own pool, latency-critical paths that
+// must not hit the implicit device synchronisation of an allocation, or
+// embedded hosts with a fixed memory budget.  This entry point serves them:
+// the digit planes that fgemm_modp keeps in context workspace live instead in
+// a file-scope __device__ array of kNoAllocScratchBytes (32 MiB) that every
+// GPU loading the library holds until the process exits.
+//
+// The host refers to that array only through its device address, obtained
+// once per device with cudaGetSymbolAddress while that device is current;
+// the first call on a device performs this set-up, so make it before any
+// stream capture.  Every call reuses the same array (the previous contents
+// remain; the packing pass rewrites every byte the kernel reads and the
+// error word is cleared on the call's stream), so calls that overlap on the
+// GPU - concurrent streams, or several host threads - race on it.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+__device__ int g_noalloc_err;
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;
+  int* err = nullptr;
+};
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+int noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return PLUQ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void* s = nullptr;
+    void* e = nullptr;
+    if (cudaGetSymbolAddress(&s, g_noalloc_scratch) != cudaSuccess ||
+        cudaGetSymbolAddress(&e, g_noalloc_err) != cudaSuccess) {
+      cudaGetLastError();
+      return PLUQ_ERR_CUDA;
+    }
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<1>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<2>::kSmem));
+    d.scratch = static_cast<unsigned char*>(s);
+    d.err = static_cast<int*>(e);
+    d.ready = true;
+  }
+  *out = &d;
+  return PLUQ_OK;
+}
+
+template <int L>
+int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int64_t M, int64_t N,
+                int64_t K, const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                uint32_t* C, int64_t ldc, cudaStream_t s) {
+  using Cfg = LimbCfg<L>;
+  const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, kTN) * kTN, Kp = cdiv(K, kTK) * kTK;
+  const size_t abytes = sizeof(__half) * L * Mp * Kp, bbytes = sizeof(__half) * L * Np * Kp;
+  const size_t aoff = ((abytes + 1023) / 1024) * 1024;
+  if (aoff + bbytes > kNoAllocScratchBytes) return PLUQ_ERR_TOO_LARGE;
+  if (cdiv(Np, 32) > 65535 || Mp / kTM > 65535) return PLUQ_ERR_TOO_LARGE;
+  __half* Ap = reinterpret_cast<__half*>(d.scratch);
+  __half* Bp = reinterpret_cast<__half*>(d.scratch + aoff);
+  PLUQ_CUDA(cudaMemsetAsync(d.err, 0, sizeof(int), s));
+  dim3 g((unsigned)std::min<int64_t>(cdiv(Kp, 256), 64), (unsigned)std::min<int64_t>(Mp, 65535));
+  k_pack_rows<L><<<g, 256, 0, s>>>(A, lda, M, K, Mp, Kp, F.p, Ap);
+  dim3 g2((unsigned)cdiv(Kp, 32), (unsigned)cdiv(Np, 32));
+  k_pack_cols<L><<<g2, dim3(32, 8), 0, s>>>(B, ldb, K, N, Np, Kp, F.p, Bp);
+  PLUQ_CUDA(cudaGetLastError());
+  CUtensorMap ma, mb;
+  PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp));
+  PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp));
+  const dim3 grid((unsigned)(Np / kTN), (unsigned)(Mp / kTM));
+  k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, s>>>(ma, mb, M, N, (int)Mp, (int)Np,
+                                                         (int)(Kp / kTK), pl.group_kb, C, ldc, F,
+                                                         pl.bias, d.err);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+}  // namespace
+
+extern "C" int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+                                  int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C,
+                                  int64_t ldc, void* stream) {
+  if (M < 0 || N < 0 || K < 0) return PLUQ_ERR_INVALID_ARG;
+  if (M == 0 || N == 0 || K == 0) return PLUQ_OK;
+  if (!A || !B || !C || lda < K || ldb < N || ldc < N) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(check_prime_range(p));
+  const LimbPlan pl = plan_for(p);
+  if (pl.L == 0) return PLUQ_ERR_UNSUPPORTED_FORM;
+  int dev = 0;
+  PLUQ_CUDA(cudaGetDevice(&dev));
+  NoAllocDevice* d = nullptr;
+  PLUQ_TRY(noalloc_setup(dev, &d));
+  const FieldP F = make_field(p);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (pl.L == 1) return noalloc_run<1>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
+  return noalloc_run<2>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
 }
