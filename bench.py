@@ -33,9 +33,11 @@ import workloads  # noqa: E402
 WORKLOAD = "lru-8192-r4096-p131071"
 METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-exact"
 
-# DRAM traffic per launch of the dominant kernel from the committed ncu capture
-# (profiles/), None until a capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {}
+# DRAM traffic (read + write bytes) per launch of each kernel class from the
+# committed ncu captures (profiles/); None where no capture of the current kernel
+# exists.  The leaf figure was captured on a 1024x1024 leaf and scaled by the
+# element count to the 2048x2048 leaves of this workload.
+NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 4.36e6 * 4.0}
 
 
 def field_ops(m: int, n: int, r: int) -> float:
