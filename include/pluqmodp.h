@@ -163,6 +163,31 @@ int pluq_last_rank(pluq_ctx* ctx, int64_t* rank);
  * value. */
 int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 
+/* Options of the recursion (value ranges in brackets):
+ *   PLUQ_OPT_LEAF_DIM    largest leaf block, rows and columns [0, 2048]
+ *                        (default 1024); 0 sends the recursion down to
+ *                        one-CTA tiles
+ *   PLUQ_OPT_LEAF_KIND   leaf kernel [0, 2]: 0 one grid barrier per pivot
+ *                        (rows dealt cyclically over the CTAs), 1 block-row
+ *                        wavefront (each CTA applies the earlier CTAs'
+ *                        pivot rows as they are published, then factors its
+ *                        own rows; one hand-off per CTA; faster on dense
+ *                        blocks), 2 (default) wavefront while the previous
+ *                        leaf of the call had rank density above 1/2, else
+ *                        barrier
+ *   PLUQ_OPT_TILE_M/N    one-CTA base-case tile [1, 128]
+ *   PLUQ_OPT_TRSM_BLOCK  diagonal block of the triangular solves [1, 64]
+ *   PLUQ_OPT_CHAIN_ROWS  rows per CTA of wavefront leaves [0, 32]; 0 (default)
+ *                        spreads the leaf over all SMs
+ * Errors: INVALID_ARG for an unknown option or a value out of range. */
+#define PLUQ_OPT_LEAF_DIM 1
+#define PLUQ_OPT_LEAF_KIND 2
+#define PLUQ_OPT_TILE_M 3
+#define PLUQ_OPT_TILE_N 4
+#define PLUQ_OPT_TRSM_BLOCK 5
+#define PLUQ_OPT_CHAIN_ROWS 6
+int pluq_set_option(pluq_ctx* ctx, int option, int value);
+
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a
  * cooperative grid over all SMs (pivot search and elimination with one grid
  * barrier per pivot); 0 disables leaves so the recursion descends to

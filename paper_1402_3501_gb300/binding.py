@@ -35,7 +35,7 @@ SYMBOLS = [
     "pluq_create", "pluq_destroy", "pluq_modp", "echelon_modp", "rank_profile_modp",
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
     "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
-    "fgemm_modp_noalloc",
+    "fgemm_modp_noalloc", "pluq_set_option",
 ]
 
 
@@ -69,6 +69,7 @@ def load():
         "pluq_status_string": [i32],
         "pluq_profile_enable": [vp, i32],
         "pluq_set_leaf": [vp, i32],
+        "pluq_set_option": [vp, i32, i32],
         "fgemm_modp_noalloc": [u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp],
         "pluq_profile_read": [vp, i32, vp, vp, vp, vp, vp],
     }
@@ -136,6 +137,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    OPTIONS = {"leaf_dim": 1, "leaf_kind": 2, "tile_m": 3, "tile_n": 4, "trsm_block": 5,
+               "chain_rows": 6}
+
+    def set_option(self, name: str, value: int):
+        """Set a recursion option (see PLUQ_OPT_* in include/pluqmodp.h)."""
+        _check(load().pluq_set_option(self.handle, self.OPTIONS[name], int(value)),
+               "pluq_set_option")
 
     def set_leaf(self, leaf_dim: int):
         """Largest block factored by one cooperative leaf launch (0: one-CTA tiles only)."""

@@ -212,10 +212,17 @@ struct Recursion {
       PLUQ_TRY(launch_iota(c, pc, n));
       return PLUQ_OK;
     }
-    const bool leaf = c->leaf_dim > 0 && leaf_fits(c, m, n);
-    if (leaf || (m <= c->bm && n <= c->bn)) {
+    // wavefront leaves win on dense blocks, barrier leaves on rank-deficient
+    // ones; kind 2 guesses from the rank density of the previous leaf
+    const bool want_chain =
+        c->leaf_kind == 1 || (c->leaf_kind == 2 && c->leaf_density > 0.5);
+    const bool chain = c->leaf_dim > 0 && want_chain && chain_fits(c, m, n);
+    const bool leaf = !chain && c->leaf_dim > 0 && leaf_fits(c, m, n);
+    if (chain || leaf || (m <= c->bm && n <= c->bn)) {
       c->n_base++;
-      if (leaf)
+      if (chain)
+        PLUQ_TRY(launch_leaf_chain(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      else if (leaf)
         PLUQ_TRY(launch_leaf_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
       else
         PLUQ_TRY(launch_base_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
@@ -225,6 +232,7 @@ struct Recursion {
       PLUQ_CUDA(cudaStreamSynchronize(c->stream));
       if (c->host_small[16] != 0) return c->host_small[16];
       *r_out = c->host_small[8];
+      if (chain || leaf) c->leaf_density = (double)*r_out / (double)std::min(m, n);
       return PLUQ_OK;
     }
     if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
@@ -340,6 +348,7 @@ int prepare(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, int form, void* strea
   c->F = make_field(p);
   c->form = f;
   c->n_base = c->n_nodes = c->n_gemm = 0;
+  c->leaf_density = 1.0;
   (void)m;
   (void)n;
   return PLUQ_OK;
@@ -597,6 +606,38 @@ int pluq_set_tuning(pluq_ctx* c, int bm, int bn, int trsm_block) {
   if (bn) c->bn = bn;
   if (trsm_block) c->trsm_block = trsm_block;
   return PLUQ_OK;
+}
+
+int pluq_set_option(pluq_ctx* c, int option, int value) {
+  if (!c) return PLUQ_ERR_INVALID_ARG;
+  switch (option) {
+    case PLUQ_OPT_LEAF_DIM:
+      if (value < 0 || value > leaf_max_dim()) return PLUQ_ERR_INVALID_ARG;
+      c->leaf_dim = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_LEAF_KIND:
+      if (value < 0 || value > 2) return PLUQ_ERR_INVALID_ARG;
+      c->leaf_kind = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_TILE_M:
+      if (value < 1 || value > 128) return PLUQ_ERR_INVALID_ARG;
+      c->bm = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_TILE_N:
+      if (value < 1 || value > 128) return PLUQ_ERR_INVALID_ARG;
+      c->bn = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_CHAIN_ROWS:
+      if (value < 0 || value > 32) return PLUQ_ERR_INVALID_ARG;
+      c->chain_rows = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_TRSM_BLOCK:
+      if (value < 1 || value > 64) return PLUQ_ERR_INVALID_ARG;
+      c->trsm_block = value;
+      return PLUQ_OK;
+    default:
+      return PLUQ_ERR_INVALID_ARG;
+  }
 }
 
 int pluq_set_leaf(pluq_ctx* c, int leaf_dim) {

@@ -17,6 +17,7 @@
 // perm_r / perm_c / rank_out as local index vectors.  The grid barrier spins
 // with a time limit; on expiry the kernel records PLUQ_ERR_TIMEOUT, raises an
 // abort flag seen by every CTA and returns without writing the block.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -328,4 +329,342 @@ int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_
   PLUQ_CUDA(cudaLaunchCooperativeKernel((const void*)k_leaf_pluq, dim3(G), dim3(kLeafThreads), args,
                                         smem, c->stream));
   return PLUQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Wavefront leaf: the same rank-profile elimination with rows distributed in
+// consecutive blocks (CTA c owns rows [c R, c R + R)).  Pivots are searched
+// row by row in row order (Sec. 4.1), so CTA c's pivots are all found after
+// those of CTAs < c.  A CTA first applies, in pivot order and as they are
+// published, the pivot rows of all earlier CTAs to its own rows (several at a
+// time, one reduction per element and batch); once every earlier CTA is done
+// it factors its own rows, publishing each pivot row (pivot-column entries
+// zeroed) with its column and inverse, then hands over with one release
+// store.  A single 64-bit word, (CTAs done << 32) | pivots published, is the
+// only synchronisation: one hand-off per CTA instead of one grid barrier per
+// pivot.  Waits are bounded; on expiry PLUQ_ERR_TIMEOUT is recorded, an abort
+// flag stops every CTA and the block is not written.
+namespace {
+
+struct ChainSync {
+  unsigned long long word;
+  int abort;
+  int pad[61];
+};
+
+struct PivInfo {
+  int row;
+  int col;
+  uint32_t inv_m;
+  int pad;
+};
+
+constexpr int kChainBatch = 8;  // pivot rows applied per pass
+
+__device__ __forceinline__ unsigned long long chain_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void chain_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <bool kIs2>
+__device__ __forceinline__ uint32_t ch_mulm(uint32_t cm, uint32_t w, const FieldP& F) {
+  if (kIs2) return cm & w;
+  return f_redc((uint64_t)cm * w, F);
+}
+
+// Block-wide minimum of v (all threads get it); red holds kLeafWarps ints.
+__device__ __forceinline__ int block_min(int v, int* red) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int out = INT_MAX;
+  for (int w = 0; w < kLeafWarps; ++w) out = min(out, red[w]);
+  return out;
+}
+
+template <bool kIs2>
+__global__ void __launch_bounds__(kLeafThreads, 1)
+    k_leaf_chain(uint32_t* __restrict__ X, int64_t ldx, int m, int n, int R, FieldP F,
+                 const uint32_t* __restrict__ inv_table, int32_t* __restrict__ perm_r,
+                 int32_t* __restrict__ perm_c, int32_t* __restrict__ rank_out, ChainSync* sync,
+                 uint32_t* __restrict__ pub, PivInfo* __restrict__ pinfo, int* __restrict__ err) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ unsigned long long s_word;
+  __shared__ int s_red[kLeafWarps];
+  __shared__ int s_col[kChainBatch];
+  __shared__ uint32_t s_inv[kChainBatch];
+  __shared__ uint32_t s_cm[kChainBatch * 32];  // multipliers per (batch pivot, row < 32)
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int mn = min(m, n);
+  const int r0 = cta * R;
+  const int own = max(0, min(R, m - r0));
+  const int ubuf = max(kChainBatch * n, 3 * m + n);  // U, reused by the output phase
+  uint32_t* W = sm;                                                 // [R][n]
+  uint32_t* U = W + (size_t)R * n;                                  // [kChainBatch][n]
+  int32_t* ispiv = reinterpret_cast<int32_t*>(U + ubuf);           // [n]
+  int32_t* rowpos = reinterpret_cast<int32_t*>(U);                  // [m]   (output phase)
+  int32_t* rowinv = rowpos + m;                                     // [m]
+  int32_t* isprow = rowinv + m;                                     // [m]
+  int32_t* colpos = isprow + m;                                     // [n]
+
+  for (int lr = warp; lr < own; lr += kLeafWarps) {
+    const uint32_t* src = X + (int64_t)(r0 + lr) * ldx;
+    for (int j = lane; j < n; j += 32) W[(size_t)lr * n + j] = src[j];
+  }
+  for (int j = tid; j < n; j += kLeafThreads) ispiv[j] = 0;
+  __syncthreads();
+
+  // wait until `cond(word)`; false on abort / timeout
+  auto wait_word = [&](int need_done, int need_piv) -> bool {
+    if (tid == 0) {
+      unsigned long long w = chain_acquire(&sync->word);
+      const long long t0 = clock64();
+      bool ok = true;
+      while ((int)(w >> 32) < need_done && (int)(w & 0xffffffffu) < need_piv) {
+        if (ld_volatile_i(&sync->abort) || clock64() - t0 > kBarrierCycles) {
+          if (!ld_volatile_i(&sync->abort)) atomicExch(err, PLUQ_ERR_TIMEOUT);
+          atomicExch(&sync->abort, 1);
+          ok = false;
+          break;
+        }
+        w = chain_acquire(&sync->word);
+      }
+      s_word = ok ? w : ~0ull;
+    }
+    __syncthreads();
+    return s_word != ~0ull;
+  };
+
+  // phase 1: apply the pivots of earlier CTAs as they are published
+  int applied = 0;
+  bool ok = true;
+  while (true) {
+    if (!wait_word(cta, applied + 1)) {
+      ok = false;
+      break;
+    }
+    const unsigned long long w = s_word;
+    const int npub = (int)(w & 0xffffffffu);
+    const int done = (int)(w >> 32);
+    while (applied < npub) {
+      const int K = min(kChainBatch, npub - applied);
+      // pivot rows (pivot-column entries already zero) and their columns
+      for (int idx = tid; idx < K * n; idx += kLeafThreads) {
+        const int kk = idx / n, j = idx - kk * n;
+        U[(size_t)kk * n + j] = __ldcg(pub + (size_t)(applied + kk) * n + j);
+      }
+      if (tid < K) {
+        const int4 pi = __ldcg(reinterpret_cast<const int4*>(pinfo + applied + tid));
+        s_col[tid] = pi.y;
+        s_inv[tid] = (uint32_t)pi.z;
+      }
+      __syncthreads();
+      // multipliers of each own row by forward substitution on the K pivot
+      // columns (one thread per row)
+      for (int lr0 = 0; lr0 < own; lr0 += 32) {
+        if (tid < 32 && lr0 + tid < own) {
+          const uint32_t* Wl = W + (size_t)(lr0 + tid) * n;
+          uint32_t cmv[kChainBatch];
+          for (int kk = 0; kk < K; ++kk) {
+            uint32_t v = Wl[s_col[kk]];
+            for (int q = 0; q < kk; ++q)
+              v = f_sub(v, ch_mulm<kIs2>(cmv[q], U[(size_t)q * n + s_col[kk]], F), F);
+            const uint32_t cmul = ch_mulm<kIs2>(s_inv[kk], v, F);
+            cmv[kk] = f_to_mont(cmul, F);
+            s_cm[kk * 32 + tid] = cmv[kk];
+          }
+        }
+        __syncthreads();
+        // W[l][j] -= sum_k c_k U_k[j]  (one Montgomery reduction per element)
+        const int rows = min(32, own - lr0);
+        for (int idx = tid; idx < rows * n; idx += kLeafThreads) {
+          const int rr = idx / n, j = idx - rr * n;
+          uint32_t* wp = W + (size_t)(lr0 + rr) * n + j;
+          uint32_t sub;
+          if (kIs2) {
+            uint32_t s2 = 0;
+            for (int kk = 0; kk < K; ++kk) s2 ^= s_cm[kk * 32 + rr] & U[(size_t)kk * n + j];
+            sub = s2;
+          } else if (K * (uint64_t)F.p < (1ull << 32)) {
+            uint64_t acc = 0;
+            for (int kk = 0; kk < K; ++kk) acc += (uint64_t)s_cm[kk * 32 + rr] * U[(size_t)kk * n + j];
+            sub = f_redc(acc, F);
+          } else {
+            sub = 0;
+            for (int kk = 0; kk < K; ++kk)
+              sub = f_add(sub, f_redc((uint64_t)s_cm[kk * 32 + rr] * U[(size_t)kk * n + j], F), F);
+          }
+          *wp = f_sub(*wp, sub, F);
+        }
+        __syncthreads();
+        // store the multipliers (plain form) at the pivot columns
+        for (int idx = tid; idx < rows * K; idx += kLeafThreads) {
+          const int rr = idx / K, kk = idx - rr * K;
+          const uint32_t cm = s_cm[kk * 32 + rr];
+          W[(size_t)(lr0 + rr) * n + s_col[kk]] = kIs2 ? cm : f_redc((uint64_t)cm, F);
+        }
+        __syncthreads();
+      }
+      for (int kk = tid; kk < K; kk += kLeafThreads) ispiv[s_col[kk]] = 1;
+      __syncthreads();
+      applied += K;
+    }
+    if (done >= cta) break;
+  }
+
+  // phase 2: factor the own rows in order (every earlier pivot is applied)
+  int np = applied;
+  if (ok) {
+    for (int lr = 0; lr < own && np < mn; ++lr) {
+      uint32_t* Wl = W + (size_t)lr * n;
+      int jl = INT_MAX;
+      for (int j = tid; j < n; j += kLeafThreads)
+        if (!ispiv[j] && Wl[j] != 0u) {
+          jl = j;
+          break;
+        }
+      const int j0 = block_min(jl, s_red);
+      if (j0 == INT_MAX) continue;  // the row reduced to zero
+      const uint32_t inv = f_inv(Wl[j0], F, inv_table);
+      const uint32_t inv_m = f_to_mont(inv, F);
+      // publish the pivot row with its pivot-column entries zeroed
+      uint32_t* dst = pub + (size_t)np * n;
+      for (int j = tid; j < n; j += kLeafThreads) {
+        const uint32_t v = ispiv[j] ? 0u : Wl[j];
+        U[j] = v;
+        dst[j] = v;
+      }
+      if (tid == 0) pinfo[np] = PivInfo{r0 + lr, j0, inv_m, 0};
+      __syncthreads();
+      if (tid == 0) {
+        ispiv[j0] = 1;
+        __threadfence();
+        chain_release(&sync->word, ((unsigned long long)cta << 32) | (unsigned)(np + 1));
+      }
+      // eliminate the own rows below it
+      for (int l2 = lr + 1 + warp; l2 < own; l2 += kLeafWarps) {
+        uint32_t* W2 = W + (size_t)l2 * n;
+        const uint32_t wl = W2[j0];
+        __syncwarp();
+        if (wl == 0u) continue;
+        const uint32_t cmul = ch_mulm<kIs2>(inv_m, wl, F);
+        const uint32_t cm = f_to_mont(cmul, F);
+        for (int j = lane; j < n; j += 32) W2[j] = f_sub(W2[j], ch_mulm<kIs2>(cm, U[j], F), F);
+        __syncwarp();
+        if (lane == 0) W2[j0] = cmul;
+      }
+      __syncthreads();
+      ++np;
+    }
+    if (tid == 0) {
+      __threadfence();
+      chain_release(&sync->word, ((unsigned long long)(cta + 1) << 32) | (unsigned)np);
+    }
+  }
+
+  // phase 3: once every CTA is done, write the own rows in the (P, Q) frame
+  if (!ok || !wait_word(G, INT_MAX)) return;
+  const int r = (int)(s_word & 0xffffffffu);
+  for (int i = tid; i < m; i += kLeafThreads) isprow[i] = 0;
+  for (int j = tid; j < n; j += kLeafThreads) ispiv[j] = 0;
+  __syncthreads();
+  for (int k = tid; k < r; k += kLeafThreads) {
+    const int4 pi = __ldcg(reinterpret_cast<const int4*>(pinfo + k));
+    isprow[pi.x] = 1;
+    ispiv[pi.y] = 1;
+    rowpos[k] = pi.x;
+    colpos[k] = pi.y;
+  }
+  __syncthreads();
+  compact_unflagged(isprow, m, rowpos, r, s_red);
+  compact_unflagged(ispiv, n, colpos, r, s_red);
+  for (int t = tid; t < m; t += kLeafThreads) rowinv[rowpos[t]] = t;
+  __syncthreads();
+  for (int lr = warp; lr < own; lr += kLeafWarps) {
+    const int t = rowinv[r0 + lr];
+    uint32_t* dst = X + (int64_t)t * ldx;
+    const uint32_t* src = W + (size_t)lr * n;
+    for (int u = lane; u < n; u += 32) dst[u] = (t >= r && u >= r) ? 0u : src[colpos[u]];
+  }
+  if (cta == 0) {
+    for (int t = tid; t < m; t += kLeafThreads) perm_r[t] = rowpos[t];
+    for (int u = tid; u < n; u += kLeafThreads) perm_c[u] = colpos[u];
+    if (tid == 0) rank_out[0] = r;
+  }
+}
+
+__global__ void k_chain_init(ChainSync* s) {
+  s->word = 0ull;
+  s->abort = 0;
+}
+
+size_t chain_smem(int m, int n, int R) {
+  const size_t ubuf = std::max<size_t>((size_t)kChainBatch * n, 3 * (size_t)m + n);
+  return sizeof(uint32_t) * ((size_t)R * n + ubuf + n);
+}
+
+}  // namespace
+
+// Rows per CTA of a wavefront leaf: as many as shared memory and the 32-row
+// bookkeeping allow up to `chain_rows` (fewer CTAs, fewer hand-offs), at
+// least enough to cover m with one CTA per SM; 0 when m does not fit.
+int chain_rows(pluq_ctx* c, int m, int n) {
+  int rmax = 32;
+  while (rmax > 0 && chain_smem(m, n, rmax) > 220 * 1024) --rmax;
+  const int rmin = (m + c->sm_count - 1) / c->sm_count;
+  if (rmax < 1 || rmin > rmax) return 0;
+  int R = c->chain_rows > 0 ? c->chain_rows : rmin;
+  if (R > rmax) R = rmax;
+  if (R < rmin) R = rmin;
+  if (R > m) R = m;
+  return R < 1 ? 1 : R;
+}
+
+int launch_leaf_chain(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
+                      int32_t* perm_c, int32_t* rank_out) {
+  static bool attr = false;
+  if (!attr) {
+    PLUQ_CUDA(cudaFuncSetAttribute(k_leaf_chain<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_leaf_chain<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr = true;
+  }
+  int R = chain_rows(c, m, n);
+  if (R < 1) return PLUQ_ERR_INVALID_ARG;
+  const int G = (m + R - 1) / R;
+  const size_t smem = chain_smem(m, n, R);
+  if (smem > 220 * 1024) return PLUQ_ERR_INVALID_ARG;
+  const int mn = m < n ? m : n;
+  const size_t head = sizeof(ChainSync);
+  const size_t need = head + sizeof(PivInfo) * mn + sizeof(uint32_t) * (size_t)mn * n + 256;
+  PLUQ_TRY(c->leaf.ensure(need));
+  ChainSync* sync = c->leaf.as<ChainSync>();
+  PivInfo* pinfo = reinterpret_cast<PivInfo*>(c->leaf.as<char>() + head);
+  uint32_t* pub = reinterpret_cast<uint32_t*>(c->leaf.as<char>() + head + sizeof(PivInfo) * mn);
+  {
+    ProfScope pi(c, PC_INDEX);
+    k_chain_init<<<1, 1, 0, c->stream>>>(sync);
+  }
+  int* err = c->small.as<int>() + 16;
+  const uint32_t* tab = inv_table_ptr(c);
+  FieldP F = c->F;
+  void* args[] = {&X, &ldx, &m, &n, &R, &F, &tab, &perm_r, &perm_c, &rank_out, &sync, &pub,
+                  &pinfo, &err};
+  ProfScope ps(c, PC_BASE, 0, 8.0 * m * n);
+  const void* fn = F.is2 ? (const void*)k_leaf_chain<true> : (const void*)k_leaf_chain<false>;
+  PLUQ_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kLeafThreads), args, smem, c->stream));
+  return PLUQ_OK;
+}
+
+int chain_fits(pluq_ctx* c, int64_t m, int64_t n) {
+  if (m <= 0 || n <= 0 || m > c->leaf_dim || n > c->leaf_dim) return 0;
+  return chain_rows(c, (int)m, (int)n) > 0;
 }

@@ -32,17 +32,23 @@ def ctx():
 
 
 class leaf_mode:
-    """Temporarily set the leaf size (0: one-CTA tiles) and base tiles."""
+    """Temporarily set the leaf size and kind (leaf 0: one-CTA tiles) and base tiles.
+
+    `leaf` is an int (wavefront leaves of that size) or a (size, kind) pair.
+    """
 
     def __init__(self, ctx, leaf, tiles=(128, 128), trsm_block=64):
-        self.ctx, self.leaf, self.tiles, self.tb = ctx, leaf, tiles, trsm_block
+        self.leaf, self.kind = (leaf if isinstance(leaf, tuple) else (leaf, 1))
+        self.ctx, self.tiles, self.tb = ctx, tiles, trsm_block
 
     def __enter__(self):
-        self.ctx.set_leaf(self.leaf)
+        self.ctx.set_option("leaf_dim", self.leaf)
+        self.ctx.set_option("leaf_kind", self.kind)
         self.ctx.set_tuning(self.tiles[0], self.tiles[1], self.tb)
 
     def __exit__(self, *exc):
-        self.ctx.set_leaf(2048)
+        self.ctx.set_option("leaf_dim", 1024)
+        self.ctx.set_option("leaf_kind", 2)
         self.ctx.set_tuning(128, 128, 64)
 
 
@@ -131,7 +137,7 @@ SHAPES = [(1, 1), (1, 40), (40, 1), (17, 33), (128, 128), (129, 130), (200, 300)
           (513, 257)]
 
 
-@pytest.mark.parametrize("leaf", [2048, 0])
+@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 2), (0, 0)])
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("p", [2, 3, 65521, 131071])
 @pytest.mark.parametrize("shape", SHAPES)
@@ -142,7 +148,7 @@ def test_pluq_uniform(ctx, leaf, form, p, shape):
         assert_parity(ctx, A, p, form)
 
 
-@pytest.mark.parametrize("leaf", [2048, 96, 0])
+@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (96, 1), (96, 0), (96, 2), (0, 0)])
 @pytest.mark.parametrize("p", [3, 131071])
 @pytest.mark.parametrize("shape", [(64, 64), (150, 200), (300, 260), (513, 257), (700, 700)])
 @pytest.mark.parametrize("frac", [0.0, 0.1, 0.5, 0.9])
@@ -156,7 +162,9 @@ def test_pluq_prescribed_rank(ctx, leaf, p, shape, frac):
 
 
 @pytest.mark.parametrize("mode", [(0, (8, 8)), (0, (16, 8)), (0, (5, 13)), (0, (32, 32)),
-                                  (0, (128, 64)), (9, (8, 8)), (24, (8, 8)), (40, (8, 8))])
+                                  (0, (128, 64)), ((9, 0), (8, 8)), ((24, 0), (8, 8)),
+                                  ((40, 0), (8, 8)), ((9, 1), (8, 8)), ((24, 1), (8, 8)),
+                                  ((40, 1), (8, 8)), ((1, 1), (8, 8))])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_pluq_deep_recursion(ctx, mode, seed):
     # small leaves / base tiles drive many recursion levels through every block step
