@@ -143,13 +143,20 @@ int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, const uint32
                        int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc,
                        void* stream);
 
-/* Batched PLUQ of `batch` independent matrices (each as pluq_modp).
+/* Batched PLUQ of `batch` independent matrices (each as pluq_modp, in place):
+ * the batching of many small rank-deficient factorizations in one persistent,
+ * graph-captured launch.  Matrices with m, n <= 1024 are taken by CTAs of one
+ * persistent kernel from a work counter (largest first), one CTA per matrix,
+ * each running the rank-profile-revealing elimination of Sec. 4.1; the
+ * launch and its descriptor / result copies are captured once in a CUDA graph
+ * per batch size and replayed.  Larger matrices are factored one by one.
  *   m, n, lda   host int64 arrays of length batch.
  *   A, P, Q     host arrays of `batch` device pointers.
  *   ranks       host int64 array of length batch; receives the ranks.
  *   status      host int32 array of length batch (may be NULL): per-matrix
- *               status codes.
- * Returns the first failing status, else PLUQ_OK. */
+ *               status codes (ENTRY_OUT_OF_RANGE leaves that matrix as is).
+ * The call returns after the results are on the host.  Returns the first
+ * failing per-matrix status, else PLUQ_OK. */
 int pluq_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const int64_t* m,
                       const int64_t* n, uint32_t* const* A, const int64_t* lda,
                       int32_t* const* P, int32_t* const* Q, int64_t* ranks, int32_t* status,

@@ -287,10 +287,15 @@ def fgemm_modp_noalloc(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, p: int
     return C
 
 
-def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None, stream=None):
-    """Batched in-place PLUQ of a list of CUDA int32 matrices: (ranks, Ps, Qs)."""
+def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None, stream=None,
+                      return_status: bool = False):
+    """Batched in-place PLUQ of a list of CUDA int32 matrices: (ranks, Ps, Qs[, status]).
+
+    With return_status, per-matrix status codes are returned instead of
+    raising on the first failure.
+    """
     if not As:
-        return [], [], []
+        return ([], [], [], []) if return_status else ([], [], [])
     ctx = ctx or default_context(As[0].device.index)
     b = len(As)
     ms = (ctypes.c_int64 * b)()
@@ -305,7 +310,7 @@ def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None,
     for i, A in enumerate(As):
         m, n, ld = _matrix_args(A)
         ms[i], ns[i], lds[i] = m, n, ld
-        aptr[i] = A.data_ptr()
+        aptr[i] = A.data_ptr() if A.numel() else None
         P = torch.empty(max(m, 1), dtype=torch.int32, device=A.device)
         Q = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
         Ps.append(P)
@@ -314,8 +319,12 @@ def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None,
         qptr[i] = Q.data_ptr()
     st = load().pluq_modp_batched(ctx.handle, p, b, ms, ns, aptr, lds, pptr, qptr, ranks, status,
                                   _form(form), _stream_handle(stream))
+    outs = (list(ranks), [P[:ms[i]] for i, P in enumerate(Ps)],
+            [Q[:ns[i]] for i, Q in enumerate(Qs)])
+    if return_status:
+        return outs + (list(status),)
     _check(st, "pluq_modp_batched")
-    return list(ranks), [P[:ms[i]] for i, P in enumerate(Ps)], [Q[:ns[i]] for i, Q in enumerate(Qs)]
+    return outs
 
 
 def last_rank(ctx: Context) -> int:

@@ -103,6 +103,16 @@ struct pluq_ctx {
   uint32_t inv_table_p = 0;
   DevBuf work;             // a copy of A for echelon / rank-profile calls
   DevBuf leaf;             // grid-barrier words and candidate rows of leaf launches
+  DevBuf batch_dev;        // batched descriptors, order, ranks, status
+  void* batch_host = nullptr;   // pinned mirror of batch_dev
+  size_t batch_host_bytes = 0;
+  cudaGraphExec_t batch_graph = nullptr;  // captured batched launch
+  int batch_graph_count = -1;
+  int64_t batch_graph_elems = 0;
+  uint32_t batch_graph_p = 0;        // field and inverse table baked into the graph
+  const void* batch_graph_tab = nullptr;
+  DevBuf batch_scratch;    // per-CTA gather scratch of the batched kernel
+  const void* batch_graph_key = nullptr;
   int32_t* host_small = nullptr;  // pinned host scalars
   // per-call statistics (host side)
   int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
@@ -130,6 +140,12 @@ int launch_leaf_chain(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32
 int chain_fits(pluq_ctx* c, int64_t m, int64_t n);
 int leaf_max_dim();
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
+int batched_max_dim();
+int launch_batched(pluq_ctx* c, const void* descs, const int32_t* order, int count,
+                   int64_t* ranks, int32_t* status, int max_elems);
+size_t batched_desc_size();
+void batched_fill_desc(void* out, int i, uint32_t* A, int32_t* P, int32_t* Q, int64_t lda, int m,
+                       int n);
 int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t count);
 int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const int64_t* seg_len,
                    int nseg);

@@ -25,6 +25,7 @@
 // columns in their original relative order.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -498,6 +499,10 @@ int pluq_destroy(pluq_ctx* c) {
   c->small.release();
   c->inv_table.release();
   c->leaf.release();
+  c->batch_dev.release();
+  c->batch_scratch.release();
+  if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
+  if (c->batch_host) cudaFreeHost(c->batch_host);
   c->work.release();
   if (c->host_small) cudaFreeHost(c->host_small);
   delete c;
@@ -581,15 +586,136 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
                       int64_t* ranks, int32_t* status, int form, void* stream) {
   if (!c || batch < 0 || (batch > 0 && (!m || !n || !A || !lda || !P || !Q || !ranks)))
     return PLUQ_ERR_INVALID_ARG;
-  int first = PLUQ_OK;
+  if (batch == 0) return PLUQ_OK;
+  PLUQ_TRY(prepare(c, p, 1, 1, form, stream));
+  PLUQ_TRY(c->small.ensure(256));
+  PLUQ_TRY(ensure_inv_table(c));
+  // matrices within the persistent kernel's limits; the others go one by one
+  const int64_t lim = batched_max_dim();
+  std::vector<int> small, big;
+  int first_bad = PLUQ_OK;
   for (int32_t b = 0; b < batch; ++b) {
-    int st = pluq_modp(c, p, m[b], n[b], A[b], lda[b], P[b], Q[b], nullptr, nullptr, nullptr, form,
-                       stream);
+    const bool argok = m[b] >= 0 && n[b] >= 0 &&
+                       (m[b] == 0 || n[b] == 0 || (A[b] && lda[b] >= n[b])) &&
+                       (m[b] == 0 || P[b]) && (n[b] == 0 || Q[b]);
+    if (!argok) {
+      ranks[b] = -1;
+      if (status) status[b] = PLUQ_ERR_INVALID_ARG;
+      if (first_bad == PLUQ_OK) first_bad = PLUQ_ERR_INVALID_ARG;
+      continue;
+    }
+    (m[b] <= lim && n[b] <= lim ? small : big).push_back(b);
+  }
+  if (!small.empty()) {
+    const int cnt = (int)small.size();
+    // longest factorizations first
+    std::vector<int32_t> order(cnt);
+    for (int i = 0; i < cnt; ++i) order[i] = i;
+    auto work = [&](int i) {
+      const double mm = (double)m[small[i]], nn = (double)n[small[i]];
+      return mm * nn * std::min(mm, nn);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    const size_t dsz = batched_desc_size();
+    const size_t off_order = ((dsz * cnt + 255) / 256) * 256;
+    const size_t off_rank = off_order + ((sizeof(int32_t) * cnt + 255) / 256) * 256;
+    const size_t off_stat = off_rank + sizeof(int64_t) * cnt;
+    const size_t total = off_stat + sizeof(int32_t) * cnt + 256;
+    if (c->batch_host_bytes < total) {
+      if (c->batch_graph) {
+        cudaGraphExecDestroy(c->batch_graph);
+        c->batch_graph = nullptr;
+      }
+      if (c->batch_host) cudaFreeHost(c->batch_host);
+      c->batch_host = nullptr;
+      c->batch_host_bytes = 0;
+      if (cudaMallocHost(&c->batch_host, total) != cudaSuccess) {
+        cudaGetLastError();
+        return PLUQ_ERR_NO_WORKSPACE;
+      }
+      c->batch_host_bytes = total;
+    }
+    const void* old_dev = c->batch_dev.ptr;
+    PLUQ_TRY(c->batch_dev.ensure(total));
+    char* hb = static_cast<char*>(c->batch_host);
+    char* db = c->batch_dev.as<char>();
+    int max_elems = 1;
+    for (int i = 0; i < cnt; ++i) {
+      const int b = small[i];
+      batched_fill_desc(hb, i, A[b], P[b], Q[b], lda[b], (int)m[b], (int)n[b]);
+      max_elems = std::max<int64_t>(max_elems, m[b] * n[b]);
+    }
+    std::memcpy(hb + off_order, order.data(), sizeof(int32_t) * cnt);
+    // one graph per (count, workspace): H2D descriptors, persistent kernel,
+    // D2H ranks and status
+    if (c->batch_graph && (c->batch_graph_count != cnt || c->batch_graph_key != db ||
+                           old_dev != c->batch_dev.ptr || c->batch_graph_elems < max_elems ||
+                           c->batch_graph_p != c->F.p ||
+                           c->batch_graph_tab != (const void*)inv_table_ptr(c))) {
+      cudaGraphExecDestroy(c->batch_graph);
+      c->batch_graph = nullptr;
+    }
+    if (!c->batch_graph) {
+      // the gather scratch is sized (and captured) for this batch's largest matrix
+      PLUQ_TRY(c->batch_scratch.ensure(sizeof(uint32_t) * (size_t)max_elems * c->sm_count));
+      cudaStream_t cs;
+      PLUQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaStream_t saved = c->stream;
+      c->stream = cs;
+      int st = PLUQ_OK;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = PLUQ_ERR_CUDA;
+      } else {
+        if (cudaMemcpyAsync(db, hb, off_rank, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+          st = PLUQ_ERR_CUDA;
+        if (st == PLUQ_OK)
+          st = launch_batched(c, db, reinterpret_cast<const int32_t*>(db + off_order), cnt,
+                              reinterpret_cast<int64_t*>(db + off_rank),
+                              reinterpret_cast<int32_t*>(db + off_stat), max_elems);
+        if (st == PLUQ_OK &&
+            cudaMemcpyAsync(hb + off_rank, db + off_rank, off_stat - off_rank + sizeof(int32_t) * cnt,
+                            cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+          st = PLUQ_ERR_CUDA;
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess) st = PLUQ_ERR_CUDA;
+      }
+      c->stream = saved;
+      if (st == PLUQ_OK && cudaGraphInstantiate(&c->batch_graph, g, 0) != cudaSuccess)
+        st = PLUQ_ERR_CUDA;
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      cudaGetLastError();
+      if (st != PLUQ_OK) {
+        c->batch_graph = nullptr;
+        return st;
+      }
+      c->batch_graph_count = cnt;
+      c->batch_graph_key = db;
+      c->batch_graph_elems = max_elems;
+      c->batch_graph_p = c->F.p;
+      c->batch_graph_tab = inv_table_ptr(c);
+    }
+    c->launches[PC_BASE] += 1;
+    c->launches[PC_INDEX] += 1;
+    PLUQ_CUDA(cudaGraphLaunch(c->batch_graph, c->stream));
+    PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t* hr = reinterpret_cast<const int64_t*>(hb + off_rank);
+    const int32_t* hs = reinterpret_cast<const int32_t*>(hb + off_stat);
+    for (int i = 0; i < cnt; ++i) {
+      const int b = small[i];
+      ranks[b] = hr[i];
+      if (status) status[b] = hs[i];
+      if (hs[i] != PLUQ_OK && first_bad == PLUQ_OK) first_bad = hs[i];
+    }
+  }
+  for (int b : big) {
+    const int st = pluq_modp(c, p, m[b], n[b], A[b], lda[b], P[b], Q[b], nullptr, nullptr, nullptr,
+                             form, stream);
     ranks[b] = st == PLUQ_OK ? (int64_t)c->host_small[8] : -1;
     if (status) status[b] = st;
-    if (st != PLUQ_OK && first == PLUQ_OK) first = st;
+    if (st != PLUQ_OK && first_bad == PLUQ_OK) first_bad = st;
   }
-  return first;
+  return first_bad;
 }
 
 int pluq_last_rank(pluq_ctx* c, int64_t* rank) {

@@ -319,3 +319,47 @@ def test_config_lru_8192(ctx, form):
     assert not np.any(LU[r:, r:])
     assert np.all(np.diag(LU[:r, :r]) != 0)
     freivalds(g.A, cfg.p, P, Q, LU, r)
+
+
+# ------------------------------------------------------------- batched --
+
+def _batch_cases(p, seed):
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(40):
+        m, n = (int(v) for v in rng.integers(1, 300, 2))
+        r = int(rng.integers(0, min(m, n) + 1))
+        cases.append(workloads.prescribed_rank_matrix(m, n, r, p, seed=int(rng.integers(1 << 30))).A)
+    cases += [np.zeros((5, 7), np.uint32), np.eye(1, dtype=np.uint32), np.zeros((0, 4), np.uint32),
+              workloads.uniform_matrix(1, 300, p, seed), workloads.uniform_matrix(300, 1, p, seed),
+              workloads.uniform_matrix(1024, 64, p, seed), workloads.uniform_matrix(1100, 40, p, seed)]
+    return cases
+
+
+@pytest.mark.parametrize("p", [2, 65521, 131071])
+def test_batched_parity(ctx, p):
+    cases = _batch_cases(p, 3)
+    As = [to_dev(A) for A in cases]
+    for rep in range(2):  # the second call replays the captured graph
+        As = [to_dev(A) for A in cases]
+        ranks, Ps, Qs = pq.pluq_modp_batched(As, p, ctx=ctx)
+        torch.cuda.synchronize()
+        for A, Ad, r, P, Q in zip(cases, As, ranks, Ps, Qs):
+            ref = oracle.pluq(A, p)
+            assert r == ref.rank
+            P, Q = P.cpu().numpy(), Q.cpu().numpy()
+            check_rpm_from_pq(P, Q, r, ref.rpm)
+            check_pluq(A, p, P, Q, Ad.cpu().numpy().astype(np.int64), r)
+
+
+def test_batched_bad_entry_status(ctx):
+    p = 65521
+    good = workloads.prescribed_rank_matrix(50, 60, 20, p, seed=1).A
+    bad = good.copy()
+    bad[3, 4] = p + 5
+    As = [to_dev(good), to_dev(bad), to_dev(good)]
+    keep = As[1].clone()
+    ranks, Ps, Qs, status = pq.pluq_modp_batched(As, p, ctx=ctx, return_status=True)
+    torch.cuda.synchronize()
+    assert status == [0, -4, 0] and ranks[0] == ranks[2] == 20
+    assert torch.equal(As[1], keep)
