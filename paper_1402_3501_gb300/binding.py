@@ -287,6 +287,44 @@ def fgemm_modp_noalloc(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, p: int
     return C
 
 
+class BatchPlan:
+    """Marshalled arguments of pluq_modp_batched for a fixed list of matrices.
+
+    Builds the pointer/size arrays once (and the P, Q outputs) so that repeated
+    calls on the same device buffers cost one C call each.
+    """
+
+    def __init__(self, As: list, p: int, form="auto", ctx: Context | None = None):
+        self.ctx = ctx or default_context(As[0].device.index)
+        self.p, self.form, self.As = p, _form(form), As
+        b = self.batch = len(As)
+        self.ms = (ctypes.c_int64 * b)()
+        self.ns = (ctypes.c_int64 * b)()
+        self.lds = (ctypes.c_int64 * b)()
+        self.aptr = (ctypes.c_void_p * b)()
+        self.pptr = (ctypes.c_void_p * b)()
+        self.qptr = (ctypes.c_void_p * b)()
+        self.ranks = (ctypes.c_int64 * b)()
+        self.status = (ctypes.c_int32 * b)()
+        self.Ps, self.Qs = [], []
+        for i, A in enumerate(As):
+            m, n, ld = _matrix_args(A)
+            self.ms[i], self.ns[i], self.lds[i] = m, n, ld
+            self.aptr[i] = A.data_ptr() if A.numel() else None
+            P = torch.empty(max(m, 1), dtype=torch.int32, device=A.device)
+            Q = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+            self.Ps.append(P)
+            self.Qs.append(Q)
+            self.pptr[i] = P.data_ptr()
+            self.qptr[i] = Q.data_ptr()
+
+    def run(self, stream=None) -> int:
+        """One batched factorization; returns the C status (per-matrix in .status)."""
+        return load().pluq_modp_batched(self.ctx.handle, self.p, self.batch, self.ms, self.ns,
+                                        self.aptr, self.lds, self.pptr, self.qptr, self.ranks,
+                                        self.status, self.form, _stream_handle(stream))
+
+
 def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None, stream=None,
                       return_status: bool = False):
     """Batched in-place PLUQ of a list of CUDA int32 matrices: (ranks, Ps, Qs[, status]).

@@ -24,6 +24,8 @@ namespace {
 constexpr int kBatchThreads = 512;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchMax = 1024;
+constexpr int kUnroll = 8;          // row loads in flight per lane
+constexpr int kBatchCtasPerSm = 2;  // co-resident CTAs hide L2 latency
 
 struct BatchDesc {
   uint32_t* A;
@@ -90,7 +92,7 @@ __device__ __forceinline__ uint32_t bt_mulm(uint32_t cm, uint32_t w, const Field
 }
 
 template <bool kIs2>
-__global__ void __launch_bounds__(kBatchThreads, 1)
+__global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm)
     k_batched_pluq(const BatchDesc* __restrict__ descs, const int32_t* __restrict__ order,
                    int batch, int* __restrict__ counter, FieldP F,
                    const uint32_t* __restrict__ inv_table, uint32_t* __restrict__ scratch,
@@ -186,16 +188,26 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         const uint32_t cmul = bt_mulm<kIs2>(inv_m, wl, F);
         const uint32_t cm = f_to_mont(cmul, F);
         int fz = INT_MAX;
-        for (int jb = 0; jb < n; jb += 32) {
-          const int j = jb + lane;
-          bool nz = false;
-          if (j < n) {
-            const uint32_t nv = f_sub(row[j], bt_mulm<kIs2>(cm, piv[j], F), F);
-            row[j] = nv;
-            nz = nv != 0u && j != j0 && !ispiv[j];
+        // eight loads in flight per lane before the dependent updates
+        for (int jb0 = 0; jb0 < n; jb0 += 32 * kUnroll) {
+          uint32_t v[kUnroll];
+#pragma unroll
+          for (int q = 0; q < kUnroll; ++q) {
+            const int j = jb0 + 32 * q + lane;
+            v[q] = j < n ? row[j] : 0u;
           }
-          const unsigned bb = __ballot_sync(0xffffffffu, nz);
-          if (bb && fz == INT_MAX) fz = jb + __ffs(bb) - 1;
+#pragma unroll
+          for (int q = 0; q < kUnroll; ++q) {
+            const int j = jb0 + 32 * q + lane;
+            bool nz = false;
+            if (j < n) {
+              const uint32_t nv = f_sub(v[q], bt_mulm<kIs2>(cm, piv[j], F), F);
+              row[j] = nv;
+              nz = nv != 0u && j != j0 && !ispiv[j];
+            }
+            const unsigned bb = __ballot_sync(0xffffffffu, nz);
+            if (bb && fz == INT_MAX) fz = jb0 + 32 * q + __ffs(bb) - 1;
+          }
         }
         __syncwarp();
         if (lane == 0) {
@@ -251,7 +263,7 @@ int batched_max_dim() { return kBatchMax; }
 int launch_batched(pluq_ctx* c, const void* descs, const int32_t* order, int count,
                    int64_t* ranks, int32_t* status, int max_elems) {
   int* counter = c->small.as<int>() + 24;
-  const int G = c->sm_count;
+  const int G = c->sm_count * kBatchCtasPerSm;
   const size_t per = (size_t)std::max(max_elems, 1);
   PLUQ_TRY(c->batch_scratch.ensure(sizeof(uint32_t) * per * G));
   {
@@ -278,3 +290,5 @@ void batched_fill_desc(void* out, int i, uint32_t* A, int32_t* P, int32_t* Q, in
                        int n) {
   static_cast<BatchDesc*>(out)[i] = BatchDesc{A, P, Q, lda, m, n};
 }
+
+int batched_ctas_per_sm() { return kBatchCtasPerSm; }

@@ -141,6 +141,7 @@ int chain_fits(pluq_ctx* c, int64_t m, int64_t n);
 int leaf_max_dim();
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
 int batched_max_dim();
+int batched_ctas_per_sm();
 int launch_batched(pluq_ctx* c, const void* descs, const int32_t* order, int count,
                    int64_t* ranks, int32_t* status, int max_elems);
 size_t batched_desc_size();

@@ -657,7 +657,8 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
     }
     if (!c->batch_graph) {
       // the gather scratch is sized (and captured) for this batch's largest matrix
-      PLUQ_TRY(c->batch_scratch.ensure(sizeof(uint32_t) * (size_t)max_elems * c->sm_count));
+      PLUQ_TRY(c->batch_scratch.ensure(sizeof(uint32_t) * (size_t)max_elems * c->sm_count *
+                                       batched_ctas_per_sm()));
       cudaStream_t cs;
       PLUQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
       cudaStream_t saved = c->stream;
