@@ -50,15 +50,19 @@ extern "C" {
 #define PLUQ_ERR_TIMEOUT -8            /* a bounded device wait ran out */
 #define PLUQ_ERR_TOO_LARGE -9          /* exceeds the fixed scratch of fgemm_modp_noalloc */
 
-/* fgemm forms for the Schur-complement updates (Sec. 3.1).
+/* fgemm forms for the Schur-complement updates (Sec. 3.1).  Both are exact
+ * and both cover every p < 2^31.
  *   FP64:     residues embedded in doubles, products on FP64 DMMA tensor
  *             instructions, one reduction per k(p-1)^2 < 2^53 block (the
- *             paper's floating-point embedding).
- *   LIMB_F16: residues balanced and split into small signed limbs held
- *             exactly in FP16, products on tcgen05 tensor cores with FP32
- *             accumulation kept below 2^24, recombined and reduced once per
- *             block; exact, like FP64.
- *   AUTO:     LIMB_F16 where available for p, else FP64. */
+ *             paper's floating-point embedding); for p beyond about 2^24 the
+ *             operands are split into 16-bit halves and four exact products
+ *             are combined.
+ *   LIMB_F16: residues balanced and split into L signed base-2^8 digits held
+ *             exactly in FP16 (L = 1 below p = 512, 2 up to about 2^18, 3 up
+ *             to about 2^25, 4 beyond), products on tcgen05 tensor cores with
+ *             FP32 accumulation kept below 2^24, recombined and reduced once
+ *             per block.
+ *   AUTO:     LIMB_F16. */
 #define PLUQ_FORM_AUTO 0
 #define PLUQ_FORM_FP64 1
 #define PLUQ_FORM_LIMB_F16 2
@@ -130,15 +134,15 @@ int fgemm_modp(pluq_ctx* ctx, uint32_t p, int64_t M, int64_t N, int64_t K, const
  *   PLUQ_FORM_LIMB_F16; same argument layout, no context.  The digit planes
  *   live in one 32 MiB device array inside the library that each GPU loading
  *   the library keeps until process exit; problems whose planes exceed it,
- *   2 L (ceil(M/128)*128 + ceil(N/128)*128) ceil(K/64)*64 bytes with L = 2
- *   digits for p up to about 2^18 (1 for p below 512), return
+ *   2 L (ceil(M/128)*128 + ceil(N/T)*T) ceil(K/64)*64 bytes with L digits as
+ *   for PLUQ_FORM_LIMB_F16 (T = 128 for L <= 2, else 64), return
  *   PLUQ_ERR_TOO_LARGE.
  *   The first call on a device looks up that array's device address (with
  *   the device current), so make it before any stream capture.  All calls
  *   share the array: calls that overlap on the GPU (other streams, other
  *   host threads) race; issue them on one stream.
- * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM (p has no limb plan), TOO_LARGE,
- * CUDA. */
+ * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM (no limb plan; not reached for
+ * p < 2^31), TOO_LARGE, CUDA. */
 int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
                        int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc,
                        void* stream);

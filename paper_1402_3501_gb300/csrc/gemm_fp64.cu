@@ -3,7 +3,11 @@
 // (mma.sync m8n8k4 .f64), accumulated exactly and reduced mod p only when the
 // accumulated magnitude could leave the 53-bit mantissa (Sec. 3.1: sums of
 // k products of residues in [0, p) stay exact while k (p-1)^2 < 2^53; the
-// reduction is delayed to that k).
+// reduction is delayed to that k).  When even one 16-deep block of products
+// of residues would not be exact ((p-1)^2 beyond 2^49), each operand is
+// split into 16-bit halves, A = 2^16 Ah + Al, and the four products
+// Ah Bh, Ah Bl, Al Bh, Al Bl are accumulated exactly in separate passes,
+// each reduced and weighted by 2^32, 2^16, 2^16, 1 mod p.
 #include "common.cuh"
 
 namespace {
@@ -26,10 +30,17 @@ __device__ __forceinline__ double dmod(double x, double p, double pinv) {
   return r;
 }
 
+// half_a / half_b: -1 whole residue, 0 low 16 bits, 1 high bits; the reduced
+// product is multiplied by `scale` (mod p) before it is subtracted from C.
+__device__ __forceinline__ uint32_t pick_half(uint32_t v, int half) {
+  return half < 0 ? v : (half == 0 ? (v & 0xFFFFu) : (v >> 16));
+}
+
 __global__ void __launch_bounds__(kThreadsF)
     k_fgemm_fp64(int64_t M, int64_t N, int64_t K, const uint32_t* __restrict__ A, int64_t lda,
                  const uint32_t* __restrict__ B, int64_t ldb, uint32_t* __restrict__ C,
-                 int64_t ldc, uint32_t p, double pd, double pinv, int ktiles_per_reduce) {
+                 int64_t ldc, uint32_t p, double pd, double pinv, int ktiles_per_reduce,
+                 int half_a, int half_b, uint32_t scale) {
   __shared__ double As[kBMf][kBKf + 1];
   __shared__ double Bs[kBKf][kBNf + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -47,12 +58,12 @@ __global__ void __launch_bounds__(kThreadsF)
     for (int idx = tid; idx < kBMf * kBKf; idx += kThreadsF) {
       const int i = idx / kBKf, kk = idx % kBKf;
       const int64_t gi = bm + i, gk = k0 + kk;
-      As[i][kk] = (gi < M && gk < K) ? (double)A[gi * lda + gk] : 0.0;
+      As[i][kk] = (gi < M && gk < K) ? (double)pick_half(A[gi * lda + gk], half_a) : 0.0;
     }
     for (int idx = tid; idx < kBKf * kBNf; idx += kThreadsF) {
       const int kk = idx / kBNf, j = idx % kBNf;
       const int64_t gk = k0 + kk, gj = bn + j;
-      Bs[kk][j] = (gk < K && gj < N) ? (double)B[gk * ldb + gj] : 0.0;
+      Bs[kk][j] = (gk < K && gj < N) ? (double)pick_half(B[gk * ldb + gj], half_b) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -87,7 +98,8 @@ __global__ void __launch_bounds__(kThreadsF)
         const int64_t row = bm + wm + mi * 8 + g;
         const int64_t col = bn + wn + ni * 8 + q * 2 + e;
         if (row < M && col < N) {
-          const uint32_t v = (uint32_t)dmod(acc[mi][ni][e], pd, pinv);
+          uint32_t v = (uint32_t)dmod(acc[mi][ni][e], pd, pinv);
+          if (scale != 1u) v = (uint32_t)((uint64_t)v * scale % p);
           uint32_t* cp = C + row * ldc + col;
           const uint32_t cv = *cp;
           *cp = cv >= v ? cv - v : cv + p - v;
@@ -95,25 +107,22 @@ __global__ void __launch_bounds__(kThreadsF)
       }
 }
 
-// Number of 16-deep k tiles whose products can be summed exactly on top of a
-// reduced value: p + kt*16*(p-1)^2 < 2^53.  0 when not even one tile fits.
-int64_t fp64_ktiles(uint32_t p) {
+// Number of 16-deep k tiles whose products of operands bounded by `bound` can
+// be summed exactly on top of a reduced value: p + kt*16*bound^2 < 2^53.  0
+// when not even one tile fits.
+int64_t fp64_ktiles_bound(uint32_t p, double bound) {
   const double lim = 9007199254740992.0;  // 2^53
-  const double sq = (double)(p - 1) * (double)(p - 1);
+  const double sq = bound * bound;
   if (sq == 0.0) return INT64_MAX;
   const double kt = floor((lim - (double)p) / (sq * kBKf));
   return kt >= 1.0 ? (int64_t)(kt > 1e15 ? 1e15 : kt) : 0;
 }
 
-}  // namespace
+int64_t fp64_ktiles(uint32_t p) { return fp64_ktiles_bound(p, (double)(p - 1)); }
 
-int fp64_form_supported(uint32_t p) { return fp64_ktiles(p) > 0; }
-
-int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
-                   const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
-  if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
-  const int64_t kt = fp64_ktiles(c->F.p);
-  if (kt <= 0) return PLUQ_ERR_UNSUPPORTED_FORM;
+int launch_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
+                const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc, int64_t kt, int ha,
+                int hb, uint32_t scale) {
   const int64_t total_kt = cdiv(K, kBKf);
   const int per_reduce = kt >= total_kt ? 0 : (int)kt;
   const dim3 grid((unsigned)cdiv(N, kBNf), (unsigned)cdiv(M, kBMf), 1);
@@ -122,7 +131,29 @@ int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
                2.0 * cdiv(M, kBMf) * kBMf * cdiv(N, kBNf) * kBNf * cdiv(K, kBKf) * kBKf);
   k_fgemm_fp64<<<grid, kThreadsF, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->F.p,
                                                   (double)c->F.p, 1.0 / (double)c->F.p,
-                                                  per_reduce);
+                                                  per_reduce, ha, hb, scale);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
+}
+
+}  // namespace
+
+// Every p < 2^31 has an FP64 form: direct, or with 16-bit halves.
+int fp64_form_supported(uint32_t p) {
+  return fp64_ktiles(p) > 0 || fp64_ktiles_bound(p, 65535.0) > 0;
+}
+
+int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
+                   const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
+  if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
+  const uint32_t p = c->F.p;
+  const int64_t kt = fp64_ktiles(p);
+  if (kt > 0) return launch_fp64(c, M, N, K, A, lda, B, ldb, C, ldc, kt, -1, -1, 1u);
+  const int64_t kth = fp64_ktiles_bound(p, 65535.0);
+  if (kth <= 0) return PLUQ_ERR_UNSUPPORTED_FORM;
+  const uint32_t w16 = (uint32_t)((1ull << 16) % p), w32 = (uint32_t)((1ull << 32) % p);
+  PLUQ_TRY(launch_fp64(c, M, N, K, A, lda, B, ldb, C, ldc, kth, 1, 1, w32));
+  PLUQ_TRY(launch_fp64(c, M, N, K, A, lda, B, ldb, C, ldc, kth, 1, 0, w16));
+  PLUQ_TRY(launch_fp64(c, M, N, K, A, lda, B, ldb, C, ldc, kth, 0, 1, w16));
+  return launch_fp64(c, M, N, K, A, lda, B, ldb, C, ldc, kth, 0, 0, 1u);
 }

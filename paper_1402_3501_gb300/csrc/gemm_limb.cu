@@ -12,9 +12,16 @@
 // t = sum_w c_w 2^{8w} (int64, exact), reduced mod p by one Montgomery step
 // and added to a residue kept in TMEM.  The last drain writes C - residue.
 //
-// Structure (one CTA per 128 x 128 tile of C, warp-specialised):
+// Digits: L = 1 or 2 for p up to about 2^17 (classes recombined into one int64
+// and reduced once), L = 3 or 4 up to 2^31.  For L >= 3 the tile is 128 x 64
+// so that the 2L-1 class accumulators and the residue fit in the 512 TMEM
+// columns, and since the recombined t may exceed 64 bits it is formed as
+// t_lo + 2^32 t_hi (classes 0-3 and 4-6) and each part is reduced on its own.
+//
+// Structure (one CTA per 128 x TN tile of C, TN = 128 for L <= 2, else 64;
+// warp-specialised):
 //   warp 0     TMA producer: digit planes of A (128 x 64 FP16, 128B swizzle)
-//              and of B^T into a 3-stage shared-memory ring;
+//              and of B^T into a shared-memory ring (6, 3, 3 or 2 stages for L = 1..4);
 //   warp 1     TMEM allocation and the single MMA-issuing thread;
 //   warps 2-9  epilogue: two warps per TMEM lane quadrant, 64 columns each.
 // The digit planes are written by a packing pass into workspace.  Every
@@ -108,14 +115,17 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 
 // Instruction descriptor, kind::f16: F32 accumulate, F16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -156,11 +166,15 @@ __device__ __forceinline__ void tmem_wait_st() {
 
 template <int L>
 struct LimbCfg {
-  static constexpr int kStages = L == 1 ? 6 : 3;
+  static constexpr int TN = L <= 2 ? kTN : 64;    // CTA tile width (C columns)
+  static constexpr int kStages = L == 1 ? 6 : (L == 4 ? 2 : 3);
   static constexpr int kClasses = 2 * L - 1;
-  static constexpr int kStageBytes = 2 * L * kTileBytes;
-  static constexpr int kResCol = kClasses * kTN;  // residue columns in TMEM
+  static constexpr int kATile = kTileBytes;               // 128 x 64 FP16
+  static constexpr int kBTile = TN * kTK * 2;             // TN x 64 FP16
+  static constexpr int kStageBytes = L * (kATile + kBTile);
+  static constexpr int kResCol = kClasses * TN;  // residue columns in TMEM
   static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr uint32_t kIdesc = idesc_f16(TN);
 };
 
 template <int L>
@@ -168,8 +182,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     k_fgemm_limb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int64_t M, int64_t N, int Mp, int Np, int num_kb, int group_kb,
                  uint32_t* __restrict__ C, int64_t ldc, FieldP F, uint64_t bias,
-                 int* __restrict__ err) {
+                 uint64_t bias_hi, int* __restrict__ err) {
   using Cfg = LimbCfg<L>;
+  constexpr int TN = Cfg::TN;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -183,7 +198,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * TN;
   const int num_groups = (num_kb + group_kb - 1) / group_kb;
 
   if (threadIdx.x == 0) {
@@ -224,8 +239,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-          tma_load_2d(st + l * kTileBytes, &tmA, kb * kTK, l * Mp + m0, &full[s]);
-          tma_load_2d(st + (L + l) * kTileBytes, &tmB, kb * kTK, l * Np + n0, &full[s]);
+          tma_load_2d(st + l * Cfg::kATile, &tmA, kb * kTK, l * Mp + m0, &full[s]);
+          tma_load_2d(st + L * Cfg::kATile + l * Cfg::kBTile, &tmB, kb * kTK, l * Np + n0,
+                      &full[s]);
         }
         issued = kb + 1;
       }
@@ -236,7 +252,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------- MMA issuer
-      const uint32_t tacc[3] = {tmem, tmem + (uint32_t)kTN, tmem + 2u * kTN};
       for (int kb = 0; kb < num_kb; ++kb) {
         const int s = kb % Cfg::kStages;
         const int g = kb / group_kb;
@@ -256,20 +271,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
 #pragma unroll
         for (int kk = 0; kk < kTK / 16; ++kk) {
-          const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-          uint64_t da[L], db[L];
+          uint32_t seen = 0;  // classes already written in this k-step
 #pragma unroll
-          for (int l = 0; l < L; ++l) {
-            da[l] = smem_desc_sw128(st + l * kTileBytes + kk * 32);
-            db[l] = smem_desc_sw128(st + (L + l) * kTileBytes + kk * 32);
-          }
-          if (L == 1) {
-            umma_f16(tacc[0], da[0], db[0], acc);
-          } else {
-            umma_f16(tacc[0], da[0], db[0], acc);
-            umma_f16(tacc[1], da[0], db[1 % L], acc);
-            umma_f16(tacc[1], da[1 % L], db[0], 1u);
-            umma_f16(tacc[2], da[1 % L], db[1 % L], acc);
+          for (int i = 0; i < L; ++i) {
+            const uint64_t da = smem_desc_sw128(st + i * Cfg::kATile + kk * 32);
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+              const uint64_t db = smem_desc_sw128(st + L * Cfg::kATile + j * Cfg::kBTile + kk * 32);
+              const int w = i + j;
+              // the first product of each class at the start of a group overwrites
+              const uint32_t acc = (first && kk == 0 && !((seen >> w) & 1u)) ? 0u : 1u;
+              seen |= 1u << w;
+              umma_f16(tmem + (uint32_t)(w * TN), da, db, Cfg::kIdesc, acc);
+            }
           }
         }
         umma_commit(&empty[s]);
@@ -294,25 +308,40 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       tc_fence_after();
       const bool last_group = g == num_groups - 1;
 #pragma unroll 1
-      for (int ch = 0; ch < 4; ++ch) {
-        const int col = h * 64 + ch * 16;
-        uint32_t c0[16], c1[16], c2[16], res[16];
-        tmem_ld16(lane_base + col, c0);
-        if (L == 2) {
-          tmem_ld16(lane_base + kTN + col, c1);
-          tmem_ld16(lane_base + 2 * kTN + col, c2);
-        }
+      for (int ch = 0; ch < TN / 32; ++ch) {
+        const int col = h * (TN / 2) + ch * 16;
+        uint32_t c[Cfg::kClasses][16], res[16];
+#pragma unroll
+        for (int w = 0; w < Cfg::kClasses; ++w) tmem_ld16(lane_base + w * TN + col, c[w]);
         if (g > 0) tmem_ld16(lane_base + Cfg::kResCol + col, res);
         tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          int64_t t = (int64_t)__float2int_rn(__uint_as_float(c0[e]));
-          if (L == 2) {
-            t += (int64_t)__float2int_rn(__uint_as_float(c1[e])) * (1 << kLimbBits);
-            t += (int64_t)__float2int_rn(__uint_as_float(c2[e])) * (1 << (2 * kLimbBits));
+          uint32_t v;
+          if (L <= 2) {
+            int64_t t = 0;
+#pragma unroll
+            for (int w = 0; w < Cfg::kClasses; ++w)
+              t += (int64_t)__float2int_rn(__uint_as_float(c[w][e])) * (1 << (kLimbBits * w));
+            v = F.is2 ? (uint32_t)((uint64_t)(t + (int64_t)bias) & 1u)
+                      : f_redc((uint64_t)(t + (int64_t)bias), F);
+          } else {
+            // classes 0..3 and 4.. recombine into two int64 values t_lo and
+            // t_hi with t = t_lo + 2^32 t_hi; as R = 2^32,
+            // t R^{-1} = t_lo R^{-1} + t_hi = REDC(t_lo) + REDC(REDC(t_hi) R^2).
+            int64_t tlo = 0, thi = 0;
+#pragma unroll
+            for (int w = 0; w < Cfg::kClasses; ++w) {
+              const int64_t cw = (int64_t)__float2int_rn(__uint_as_float(c[w][e]));
+              if (w < 4)
+                tlo += cw * ((int64_t)1 << (kLimbBits * w));
+              else
+                thi += cw * ((int64_t)1 << (kLimbBits * (w - 4)));
+            }
+            const uint32_t vlo = f_redc((uint64_t)(tlo + (int64_t)bias), F);
+            const uint32_t vhi = f_redc((uint64_t)(thi + (int64_t)bias_hi), F);
+            v = f_add(vlo, f_redc((uint64_t)vhi * F.r2, F), F);
           }
-          const uint32_t v = F.is2 ? (uint32_t)((uint64_t)(t + (int64_t)bias) & 1u)
-                                   : f_redc((uint64_t)(t + (int64_t)bias), F);
           res[e] = g > 0 ? f_add(res[e], v, F) : v;
         }
         if (!last_group) {
@@ -321,7 +350,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           // residue holds (sum t) R^{-1}; one more step with R^2 undoes it.
           // Stage the tile in the (now idle) pipeline shared memory so that
           // C is updated with row-contiguous accesses below.
-          uint32_t* stage = reinterpret_cast<uint32_t*>(smem) + row * (kTN + 1) + col;
+          uint32_t* stage = reinterpret_cast<uint32_t*>(smem) + row * (TN + 1) + col;
 #pragma unroll
           for (int e = 0; e < 16; ++e)
             stage[e] = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
@@ -343,16 +372,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const int64_t gr = (int64_t)m0 + rr;
         if (gr >= M) break;
         uint32_t* crow = C + gr * ldc + n0;
-        uint32_t cv[kTN / 32];
+        uint32_t cv[TN / 32];
 #pragma unroll
-        for (int q2 = 0; q2 < kTN / 32; ++q2) {
+        for (int q2 = 0; q2 < TN / 32; ++q2) {
           const int j = lane + 32 * q2;
           cv[q2] = (n0 + j < N) ? crow[j] : 0u;
         }
 #pragma unroll
-        for (int q2 = 0; q2 < kTN / 32; ++q2) {
+        for (int q2 = 0; q2 < TN / 32; ++q2) {
           const int j = lane + 32 * q2;
-          if (n0 + j < N) crow[j] = f_sub(cv[q2], stage[rr * (kTN + 1) + j], F);
+          if (n0 + j < N) crow[j] = f_sub(cv[q2], stage[rr * (TN + 1) + j], F);
         }
       }
     }
@@ -435,13 +464,26 @@ __global__ void k_pack_cols(const uint32_t* __restrict__ B, int64_t ldb, int64_t
 struct LimbPlan {
   int L = 0;
   int group_kb = 0;  // K blocks of 64 per exact accumulation group
-  uint64_t bias = 0;
+  uint64_t bias = 0;     // multiple of p making the (low) recombined drain value >= 0
+  uint64_t bias_hi = 0;  // same for the high part (L >= 3)
 };
 
 // Largest |digit| of each of the L digits over all balanced residues.
 void digit_bounds(uint32_t p, int L, int64_t* bound) {
   const int64_t h = p / 2;  // balanced residues lie in [-(p/2), p/2] (p = 2: {-1, 0})
   for (int l = 0; l < L; ++l) bound[l] = 0;
+  if (L >= 3) {
+    // low digits take every value of [-2^7, 2^7); the top digit of x is
+    // floor((x + c) / 2^{8(L-1)}) with c = 2^7 (1 + 2^8 + ... + 2^{8(L-2)}),
+    // monotone in x, so its extremes sit at x = +-h
+    for (int l = 0; l < L - 1; ++l) bound[l] = (int64_t)1 << (kLimbBits - 1);
+    const int64_t base = (int64_t)1 << (kLimbBits * (L - 1));
+    const int64_t c = ((int64_t)1 << (kLimbBits - 1)) * ((base - 1) / ((1 << kLimbBits) - 1));
+    auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    const int64_t top_hi = fdiv(h + c, base), top_lo = fdiv(-h + c, base);
+    bound[L - 1] = std::max(top_hi < 0 ? -top_hi : top_hi, top_lo < 0 ? -top_lo : top_lo);
+    return;
+  }
   auto digits = [&](int64_t x) {
     for (int l = 0; l < L; ++l) {
       int64_t d;
@@ -466,11 +508,12 @@ void digit_bounds(uint32_t p, int L, int64_t* bound) {
 
 LimbPlan plan_for(uint32_t p) {
   LimbPlan pl;
-  for (int L = 1; L <= 2; ++L) {
-    int64_t b[2] = {0, 0};
+  const long double lim = (long double)p * 4294967296.0L;  // REDC input bound p R
+  for (int L = 1; L <= 4; ++L) {
+    int64_t b[4] = {0, 0, 0, 0};
     digit_bounds(p, L, b);
     // weight-class bounds: class w collects digit pairs (i, w - i)
-    int64_t cls[3] = {0, 0, 0};
+    int64_t cls[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int i = 0; i < L; ++i)
       for (int j = 0; j < L; ++j) cls[i + j] += b[i] * b[j];
     int64_t worst = 1;
@@ -480,15 +523,21 @@ LimbPlan plan_for(uint32_t p) {
     const int64_t need = L == 1 ? 4 : 1;  // L = 1 only when it needs few drains
     if (gkb < need) continue;
     const int64_t kflush = gkb * kTK;
-    // largest |t| = sum_w kflush * cls[w] * 2^(8w)
-    long double tmax = 0;
-    for (int w = 0; w < 2 * L - 1; ++w) tmax += (long double)kflush * cls[w] * powl(2.0L, 8 * w);
-    const long double lim = (long double)p * 4294967296.0L;  // REDC input bound p R
-    if (p != 2 && 2 * tmax + p >= lim) continue;
+    // largest |t| per drain: t = sum_w kflush cls[w] 2^{8w} (L <= 2); for
+    // L >= 3 the same sum split at w = 4 into t_lo and t_hi
+    long double tmax = 0, tmax_hi = 0;
+    for (int w = 0; w < 2 * L - 1; ++w) {
+      if (L >= 3 && w >= 4)
+        tmax_hi += (long double)kflush * cls[w] * powl(2.0L, 8 * (w - 4));
+      else
+        tmax += (long double)kflush * cls[w] * powl(2.0L, 8 * w);
+    }
+    if (p != 2 && (2 * tmax + p >= lim || 2 * tmax_hi + p >= lim)) continue;
     pl.L = L;
     pl.group_kb = (int)(gkb > 1 << 20 ? 1 << 20 : gkb);
-    const uint64_t tm = (uint64_t)tmax + 1;
+    const uint64_t tm = (uint64_t)tmax + 1, tmh = (uint64_t)tmax_hi + 1;
     pl.bias = p == 2 ? 0 : (tm + p - 1) / p * p;
+    pl.bias_hi = p == 2 ? 0 : (tmh + p - 1) / p * p;
     return pl;
   }
   return pl;
@@ -509,12 +558,12 @@ EncodeTiled get_encode() {
   return fn;
 }
 
-int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t kp) {
+int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t kp, int box_rows) {
   EncodeTiled enc = get_encode();
   if (!enc) return PLUQ_ERR_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -532,7 +581,8 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
                                    Cfg::kSmem));
     attr = true;
   }
-  const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, kTN) * kTN, Kp = cdiv(K, kTK) * kTK;
+  constexpr int TN = Cfg::TN;
+  const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, TN) * TN, Kp = cdiv(K, kTK) * kTK;
   if (L * Mp > INT32_MAX || L * Np > INT32_MAX || Kp > INT32_MAX) return PLUQ_ERR_INVALID_ARG;
   const size_t abytes = sizeof(__half) * L * Mp * Kp, bbytes = sizeof(__half) * L * Np * Kp;
   PLUQ_TRY(c->pack.ensure(abytes + bbytes + 1024));
@@ -547,16 +597,17 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
     PLUQ_CUDA(cudaGetLastError());
   }
   CUtensorMap ma, mb;
-  PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp));
-  PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp));
-  const dim3 grid((unsigned)(Np / kTN), (unsigned)(Mp / kTM));
+  PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp, kTM));
+  PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp, TN));
+  const dim3 grid((unsigned)(Np / TN), (unsigned)(Mp / kTM));
   if (grid.y > 65535 || cdiv(Np, 32) > 65535) return PLUQ_ERR_INVALID_ARG;
   int* err = c->small.as<int>() + 16;
   ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K,
                (double)abytes + (double)bbytes + 8.0 * M * N, 1,
                2.0 * Mp * Np * Kp * L * L);
   k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, c->stream>>>(
-      ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK), pl.group_kb, C, ldc, c->F, pl.bias, err);
+      ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK), pl.group_kb, C, ldc, c->F, pl.bias,
+      pl.bias_hi, err);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
@@ -576,6 +627,8 @@ int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
   }
   if (cached.L == 1) return run_limb<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   if (cached.L == 2) return run_limb<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  if (cached.L == 3) return run_limb<3>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  if (cached.L == 4) return run_limb<4>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   return PLUQ_ERR_UNSUPPORTED_FORM;
 }
 
@@ -628,6 +681,10 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
                                    LimbCfg<1>::kSmem));
     PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    LimbCfg<2>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<3>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<4>::kSmem));
     d.scratch = static_cast<unsigned char*>(s);
     d.err = static_cast<int*>(e);
     d.ready = true;
@@ -641,7 +698,8 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
                 int64_t K, const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
                 uint32_t* C, int64_t ldc, cudaStream_t s) {
   using Cfg = LimbCfg<L>;
-  const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, kTN) * kTN, Kp = cdiv(K, kTK) * kTK;
+  constexpr int TN = Cfg::TN;
+  const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, TN) * TN, Kp = cdiv(K, kTK) * kTK;
   const size_t abytes = sizeof(__half) * L * Mp * Kp, bbytes = sizeof(__half) * L * Np * Kp;
   const size_t aoff = ((abytes + 1023) / 1024) * 1024;
   if (aoff + bbytes > kNoAllocScratchBytes) return PLUQ_ERR_TOO_LARGE;
@@ -655,12 +713,12 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
   k_pack_cols<L><<<g2, dim3(32, 8), 0, s>>>(B, ldb, K, N, Np, Kp, F.p, Bp);
   PLUQ_CUDA(cudaGetLastError());
   CUtensorMap ma, mb;
-  PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp));
-  PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp));
-  const dim3 grid((unsigned)(Np / kTN), (unsigned)(Mp / kTM));
+  PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp, kTM));
+  PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp, TN));
+  const dim3 grid((unsigned)(Np / TN), (unsigned)(Mp / kTM));
   k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, s>>>(ma, mb, M, N, (int)Mp, (int)Np,
                                                          (int)(Kp / kTK), pl.group_kb, C, ldc, F,
-                                                         pl.bias, d.err);
+                                                         pl.bias, pl.bias_hi, d.err);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
@@ -683,5 +741,7 @@ extern "C" int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, c
   const FieldP F = make_field(p);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (pl.L == 1) return noalloc_run<1>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
-  return noalloc_run<2>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
+  if (pl.L == 2) return noalloc_run<2>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
+  if (pl.L == 3) return noalloc_run<3>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
+  return noalloc_run<4>(*d, pl, F, M, N, K, A, lda, B, ldb, C, ldc, s);
 }

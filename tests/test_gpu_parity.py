@@ -108,13 +108,44 @@ def test_fgemm_adversarial_extremes(ctx, form):
             assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), (p, K)
 
 
-def test_fgemm_unsupported_forms(ctx):
-    p = 2147483647
-    A = to_dev(np.ones((8, 8)))
-    for form in ["fp64", "limb", "auto"]:
-        with pytest.raises(pq.PluqError) as e:
-            pq.fgemm_modp(A.clone(), A, A, p, form=form, ctx=ctx)
-        assert e.value.status == -5
+# primes past the 17-bit range: the FP64 form splits into 16-bit halves (four
+# exact passes); the limb form takes three (p < 2^25) or four base-2^8 digits
+LARGE_PRIMES = [1048573, 16777213, 33554393, 268435399, 1073741789, 2147483647]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p", LARGE_PRIMES)
+@pytest.mark.parametrize("mnk", [(70, 33, 17), (129, 257, 300), (130, 70, 2000)])
+def test_fgemm_large_primes(ctx, form, p, mnk):
+    M, N, K = mnk
+    rng = np.random.default_rng(M + N + K + p % 1000)
+    A = rng.integers(0, p, (M, K), dtype=np.int64)
+    B = rng.integers(0, p, (K, N), dtype=np.int64)
+    C = rng.integers(0, p, (M, N), dtype=np.int64)
+    A[0, :] = p - 1
+    B[:, 0] = p - 1
+    expect = (C - matmul_mod(A, B, p)) % p
+    Cd = to_dev(C)
+    pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form=form, ctx=ctx)
+    torch.cuda.synchronize()
+    assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect)
+
+
+@pytest.mark.parametrize("p", [16777213, 33554393, 2147483647])
+def test_fgemm_large_primes_extremes(ctx, p):
+    # the balanced extremes +-(p-1)/2 maximise every digit-class sum of the limb form
+    h = (p - 1) // 2
+    for a, b in [(h, h), (h, h + 1), (h + 1, h + 1), (p - 1, p - 1)]:
+        for K in [319, 320, 321, 1281]:
+            A = np.full((130, K), a, dtype=np.int64)
+            B = np.full((K, 70), b, dtype=np.int64)
+            C = np.zeros((130, 70), dtype=np.int64)
+            expect = (C - matmul_mod(A, B, p)) % p
+            for form in FORMS:
+                Cd = to_dev(C)
+                pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form=form, ctx=ctx)
+                torch.cuda.synchronize()
+                assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), (form, a, b, K)
 
 
 def test_fgemm_strided_views(ctx):
@@ -159,6 +190,21 @@ def test_pluq_prescribed_rank(ctx, leaf, p, shape, frac):
     with leaf_mode(ctx, leaf):
         got = assert_parity(ctx, g.A, p)
     assert got == r
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p", [1048573, 2147483647])
+@pytest.mark.parametrize("shape,frac", [((129, 130), 1.0), ((300, 200), 1.0), ((513, 257), 0.5),
+                                        ((700, 700), 0.9)])
+def test_pluq_large_primes(ctx, form, p, shape, frac):
+    m, n = shape
+    r = int(frac * min(m, n))
+    with leaf_mode(ctx, 96, tiles=(64, 64)):
+        if frac == 1.0:
+            assert_parity(ctx, workloads.uniform_matrix(m, n, p, 5), p, form)
+        else:
+            A = workloads.prescribed_rank_matrix(m, n, r, p, 5).A
+            assert assert_parity(ctx, A, p, form) == r
 
 
 @pytest.mark.parametrize("mode", [(0, (8, 8)), (0, (16, 8)), (0, (5, 13)), (0, (32, 32)),
@@ -363,3 +409,100 @@ def test_batched_bad_entry_status(ctx):
     torch.cuda.synchronize()
     assert status == [0, -4, 0] and ranks[0] == ranks[2] == 20
     assert torch.equal(As[1], keep)
+
+
+def freivalds_f64(A, p, P, Q, LU, r, trials=2, seed=0):
+    """Exact float64 Freivalds check of A[P][:, Q] = L U mod p for p < 2^16.
+
+    Entries and vector entries below 2^16 keep every product below 2^32 and
+    every row sum of up to 2^21 terms below 2^53, so float64 sums are exact.
+    """
+    assert p < 2 ** 16
+    rng = np.random.default_rng(seed)
+    m, n = A.shape
+    step = 2048
+    for _ in range(trials):
+        x = rng.integers(0, p, n).astype(np.float64)
+        z = np.zeros(n)
+        z[Q] = x
+        lhs = np.concatenate([np.mod(A[i:i + step].astype(np.float64) @ z, p)
+                              for i in range(0, m, step)])[P]
+        # U x: U[t, u] for u >= t, t < r (rows of the compressed storage)
+        ux = np.concatenate([np.mod(np.triu(LU[i:min(r, i + step), :].astype(np.float64), i) @ x, p)
+                             for i in range(0, r, step)]) if r else np.zeros(0)
+        rhs = np.zeros(m)
+        for i in range(0, m, step):
+            rows = np.arange(i, min(m, i + step))
+            Lb = np.where(np.arange(r)[None, :] < rows[:, None],
+                          LU[i:i + step, :r].astype(np.float64), 0.0)
+            on_diag = rows < r
+            Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1.0
+            rhs[i:i + step] = np.mod(Lb @ ux, p)
+        assert np.array_equal(lhs, rhs), "Freivalds check of P L U Q = A failed"
+
+
+@pytest.mark.parametrize("form", ["limb"])
+def test_config_uniform_32768(ctx, form):
+    """Full-size 32768^2 over GF(65521): RPM on blocks the oracle can factor, Freivalds."""
+    cfg = workloads.CONFIGS["uniform-32768-p65521"]
+    m, n, p = cfg.m, cfg.n, cfg.p
+    A = workloads.uniform_matrix(m, n, p, seed=1)
+    res = pq.pluq_modp(to_dev(A), p, form=form, ctx=ctx)
+    torch.cuda.synchronize()
+    r = res.rank
+    P = res.P.cpu().numpy()
+    Q = res.Q.cpu().numpy()
+    LU = res.LU.cpu().numpy()
+    assert sorted(P.tolist()) == list(range(m)) and sorted(Q.tolist()) == list(range(n))
+    rpm = set(zip(P[:r].tolist(), Q[:r].tolist()))
+    # the rank profile matrix of a leading block is the restriction of A's
+    for (i, j) in [(1536, 1536), (192, n), (m, 160)]:
+        ref = oracle.pluq(np.ascontiguousarray(A[:i, :j]), p, want_lu=False)
+        assert {(a, b) for (a, b) in rpm if a < i and b < j} == ref.rpm, (i, j)
+    assert not np.any(LU[r:, r:])
+    assert np.all(np.diag(LU[:r, :r]) != 0)
+    freivalds_f64(A, p, P, Q, LU, r)
+
+
+def freivalds_blocked(A, p, P, Q, LU, r, trials=1, seed=0, step=1024):
+    """Freivalds check of A[P][:, Q] = L U mod p by row blocks, exact int64 for any p < 2^31."""
+    rng = np.random.default_rng(seed)
+    m, n = A.shape
+
+    def mv(X, v):
+        return matmul_mod(X, v[:, None], p)[:, 0]
+
+    for _ in range(trials):
+        x = rng.integers(0, p, n, dtype=np.int64)
+        z = np.zeros(n, dtype=np.int64)
+        z[Q] = x
+        lhs = np.concatenate([mv(A[i:i + step], z) for i in range(0, m, step)])[P]
+        ux = (np.concatenate([mv(np.triu(LU[i:min(r, i + step)].astype(np.int64), i), x)
+                              for i in range(0, r, step)]) if r else np.zeros(0, np.int64))
+        rhs = np.zeros(m, dtype=np.int64)
+        for i in range(0, m, step):
+            rows = np.arange(i, min(m, i + step))
+            Lb = np.where(np.arange(r)[None, :] < rows[:, None], LU[i:i + step, :r].astype(np.int64), 0)
+            on_diag = rows < r
+            Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1
+            rhs[i:i + step] = mv(Lb, ux)
+        assert np.array_equal(lhs, rhs), "Freivalds check of P L U Q = A failed"
+
+
+@pytest.mark.parametrize("form", ["limb"])
+def test_config_lru_16384x20480_p31(ctx, form):
+    """Full-size 16384 x 20480, rank 16320, over GF(2^31 - 1): RPM by construction, Freivalds."""
+    cfg = workloads.CONFIGS["lru-16384x20480-r16320-p2147483647"]
+    g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
+    res = pq.pluq_modp(to_dev(g.A), cfg.p, form=form, ctx=ctx)
+    torch.cuda.synchronize()
+    r = res.rank
+    P, Q = res.P.cpu().numpy(), res.Q.cpu().numpy()
+    assert r == cfg.r
+    check_rpm_from_pq(P, Q, r, g.rpm)
+    assert res.rrp.cpu().numpy().tolist() == g.rrp.tolist()
+    assert res.crp.cpu().numpy().tolist() == g.crp.tolist()
+    LU = res.LU.cpu().numpy().view(np.uint32)
+    assert not np.any(LU[r:, r:])
+    assert np.all(np.diag(LU[:r, :r]) != 0)
+    freivalds_blocked(g.A, cfg.p, P, Q, LU, r)

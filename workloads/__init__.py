@@ -74,9 +74,18 @@ class Stream:
 
 
 def uniform_matrix(m: int, n: int, p: int, seed: int, tag: str = "uniform") -> np.ndarray:
-    """m x n residues i.i.d. uniform in [0, p), uint32 row-major."""
+    """m x n residues i.i.d. uniform in [0, p), uint32 row-major.
+
+    Drawn in row blocks (one counter sequence), so large matrices need no
+    64-bit temporaries of their full size.
+    """
     s = Stream(seed, f"{tag}:{m}x{n}:p{p}")
-    return s.below(p, m * n).astype(np.uint32).reshape(m, n)
+    out = np.empty((m, n), dtype=np.uint32)
+    rows = max(1, (1 << 24) // max(n, 1))
+    for r0 in range(0, m, rows):
+        r1 = min(m, r0 + rows)
+        out[r0:r1] = s.below(p, (r1 - r0) * n).astype(np.uint32).reshape(r1 - r0, n)
+    return out
 
 
 @dataclass
