@@ -188,7 +188,8 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        barrier
  *   PLUQ_OPT_TILE_M/N    one-CTA base-case tile [1, 128]
  *   PLUQ_OPT_TRSM_BLOCK  diagonal block of the triangular solves [1, 64]
- *   PLUQ_OPT_CHAIN_ROWS  rows per CTA of wavefront leaves [0, 32]; 0 (default)
+ *                        (each block is inverted, then applied as a product)
+ *   PLUQ_OPT_CHAIN_ROWS  rows per CTA of wavefront leaves [0, 64]; 0 (default)
  *                        spreads the leaf over all SMs
  * Errors: INVALID_ARG for an unknown option or a value out of range. */
 #define PLUQ_OPT_LEAF_DIM 1

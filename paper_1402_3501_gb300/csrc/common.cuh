@@ -23,6 +23,49 @@
 
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Global-to-shared copies for latency-bound kernels: each thread keeps kIlp
+// independent L2 loads in flight before storing, instead of one dependent
+// load per loop trip.  L2-only loads (ld.global.cg) also read data that other
+// SMs wrote earlier in the same kernel.
+template <int kIlp = 8>
+__device__ __forceinline__ void copy_g2s(uint32_t* __restrict__ dst,
+                                         const uint32_t* __restrict__ src, int count, int tid,
+                                         int nthreads) {
+  int i = tid;
+  for (; i + (kIlp - 1) * nthreads < count; i += kIlp * nthreads) {
+    uint32_t v[kIlp];
+#pragma unroll
+    for (int q = 0; q < kIlp; ++q) v[q] = __ldcg(src + i + q * nthreads);
+#pragma unroll
+    for (int q = 0; q < kIlp; ++q) dst[i + q * nthreads] = v[q];
+  }
+  for (; i < count; i += nthreads) dst[i] = __ldcg(src + i);
+}
+
+// rows x n block (row stride lds) into dense shared rows, one warp per row.
+template <int kIlp = 16>
+__device__ __forceinline__ void copy_rows_g2s(uint32_t* __restrict__ dst,
+                                              const uint32_t* __restrict__ src, int64_t lds,
+                                              int rows, int n, int warp, int lane, int nwarps) {
+  for (int lr = warp; lr < rows; lr += nwarps) {
+    const uint32_t* s = src + (int64_t)lr * lds;
+    uint32_t* d = dst + (size_t)lr * n;
+    for (int j0 = lane; j0 < n; j0 += 32 * kIlp) {
+      uint32_t v[kIlp];
+#pragma unroll
+      for (int q = 0; q < kIlp; ++q) {
+        const int j = j0 + 32 * q;
+        v[q] = j < n ? __ldcg(s + j) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kIlp; ++q) {
+        const int j = j0 + 32 * q;
+        if (j < n) d[j] = v[q];
+      }
+    }
+  }
+}
+
 // A growable device allocation owned by the context.
 struct DevBuf {
   void* ptr = nullptr;
@@ -98,6 +141,7 @@ struct pluq_ctx {
   DevBuf pack;             // packed limb / fp64 GEMM operands
   DevBuf perm_r, perm_c;   // int32 [kMaxDepth][mmax], [kMaxDepth][nmax]
   DevBuf tmp_i;            // int32 scratch for segment permutations
+  DevBuf tri_inv;          // inverted diagonal blocks of a triangular solve
   DevBuf small;            // int32 / int64 scalars (rank, flags)
   DevBuf inv_table;        // uint32[p] inverses when p is small
   uint32_t inv_table_p = 0;

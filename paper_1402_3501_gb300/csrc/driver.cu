@@ -499,6 +499,7 @@ int pluq_destroy(pluq_ctx* c) {
   c->small.release();
   c->inv_table.release();
   c->leaf.release();
+  c->tri_inv.release();
   c->batch_dev.release();
   c->batch_scratch.release();
   if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
@@ -755,7 +756,7 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
       c->bn = value;
       return PLUQ_OK;
     case PLUQ_OPT_CHAIN_ROWS:
-      if (value < 0 || value > 32) return PLUQ_ERR_INVALID_ARG;
+      if (value < 0 || value > 64) return PLUQ_ERR_INVALID_ARG;
       c->chain_rows = value;
       return PLUQ_OK;
     case PLUQ_OPT_TRSM_BLOCK:

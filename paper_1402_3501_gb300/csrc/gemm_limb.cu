@@ -299,7 +299,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int h = (warp - 2) >> 2;    // column half
     const int row = q * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    const int64_t grow = (int64_t)m0 + row;
     for (int g = 0; g < num_groups; ++g) {
       if (!mbar_wait(acc_full, g & 1, err)) {
         *abort_flag = 1;

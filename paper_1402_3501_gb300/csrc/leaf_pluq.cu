@@ -133,10 +133,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
   int owned = 0;
   for (int lr = 0; lr < rown; ++lr)
     if ((int64_t)lr * G + cta < m) owned = lr + 1;
-  for (int lr = warp; lr < owned; lr += kLeafWarps) {
-    const uint32_t* src = X + ((int64_t)lr * G + cta) * ldx;
-    for (int j = lane; j < n; j += 32) W[(size_t)lr * n + j] = src[j];
-  }
+  copy_rows_g2s(W, X + (int64_t)cta * ldx, ldx * (int64_t)G, owned, n, warp, lane, kLeafWarps);
   for (int j = tid; j < n; j += kLeafThreads) ispiv[j] = 0;
   __syncthreads();
 
@@ -359,7 +356,8 @@ struct PivInfo {
   int pad;
 };
 
-constexpr int kChainBatch = 8;  // pivot rows applied per pass
+constexpr int kChainBatch = 8;     // pivot rows applied per pass
+constexpr int kChainMaxRows = 64;  // rows per CTA, at most
 
 __device__ __forceinline__ unsigned long long chain_acquire(const unsigned long long* p) {
   unsigned long long v;
@@ -414,10 +412,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
   int32_t* isprow = rowinv + m;                                     // [m]
   int32_t* colpos = isprow + m;                                     // [n]
 
-  for (int lr = warp; lr < own; lr += kLeafWarps) {
-    const uint32_t* src = X + (int64_t)(r0 + lr) * ldx;
-    for (int j = lane; j < n; j += 32) W[(size_t)lr * n + j] = src[j];
-  }
+  copy_rows_g2s(W, X + (int64_t)r0 * ldx, ldx, own, n, warp, lane, kLeafWarps);
   for (int j = tid; j < n; j += kLeafThreads) ispiv[j] = 0;
   __syncthreads();
 
@@ -456,10 +451,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
     while (applied < npub) {
       const int K = min(kChainBatch, npub - applied);
       // pivot rows (pivot-column entries already zero) and their columns
-      for (int idx = tid; idx < K * n; idx += kLeafThreads) {
-        const int kk = idx / n, j = idx - kk * n;
-        U[(size_t)kk * n + j] = __ldcg(pub + (size_t)(applied + kk) * n + j);
-      }
+      copy_g2s(U, pub + (size_t)applied * n, K * n, tid, kLeafThreads);
       if (tid < K) {
         const int4 pi = __ldcg(reinterpret_cast<const int4*>(pinfo + applied + tid));
         s_col[tid] = pi.y;
@@ -612,11 +604,12 @@ size_t chain_smem(int m, int n, int R) {
 
 }  // namespace
 
-// Rows per CTA of a wavefront leaf: as many as shared memory and the 32-row
-// bookkeeping allow up to `chain_rows` (fewer CTAs, fewer hand-offs), at
-// least enough to cover m with one CTA per SM; 0 when m does not fit.
+// Rows per CTA of a wavefront leaf: `chain_rows` within what shared memory
+// allows (default: the fewest that cover m with one CTA per SM, i.e. the
+// most CTAs, which measured fastest), at least that many; 0 when m does not
+// fit.
 int chain_rows(pluq_ctx* c, int m, int n) {
-  int rmax = 32;
+  int rmax = kChainMaxRows;
   while (rmax > 0 && chain_smem(m, n, rmax) > 220 * 1024) --rmax;
   const int rmin = (m + c->sm_count - 1) / c->sm_count;
   if (rmax < 1 || rmin > rmax) return 0;

@@ -1,114 +1,250 @@
 // Triangular solves mod p (the ftrsm of Sec. 2.1): block recursive, the
-// off-diagonal work reduced to fgemm calls and the diagonal blocks (at most
-// kTB x kTB) solved by one CTA in shared memory.
+// off-diagonal work reduced to fgemm calls.  The kTB x kTB diagonal blocks
+// are first inverted together (one launch, one CTA per block); each diagonal
+// solve is then a small dense product with its inverse, parallel over all the
+// right-hand sides and their rows (no sequential substitution chain).
 //
 //   trsm_left_lower_unit : B <- L^{-1} B   (L unit lower, r x r)   D, O
 //   trsm_right_upper     : B <- B U^{-1}   (U upper, r x r)        E, [I; K]
 //   trsm_left_upper      : B <- U^{-1} B   (U upper, r x r)        RREF
-//
-// Non-unit triangles are first made unit by scaling with the inverses of
-// their diagonal (U = D U' with U' unit upper), so the substitution loop
-// needs no division: X U = B  <=>  (X D) U' = B, and U X = B  <=>
-// U'' X = D^{-1} B with U'' = D^{-1} U.
+
 #include "common.cuh"
 
 namespace {
 
-constexpr int kTB = 64;       // diagonal block
-constexpr int kStrip = 64;    // columns (or rows) of B per CTA
-constexpr int kTrsmThreads = 256;
+constexpr int kTB = 64;  // diagonal block
 
-// B (r x ncols) <- L^{-1} B, L unit lower r x r, r <= kTB; one CTA per strip
-// of kStrip columns.
-__global__ void __launch_bounds__(kTrsmThreads)
-    k_trsm_llu_small(const uint32_t* __restrict__ L, int64_t ldl, int r, uint32_t* __restrict__ B,
-                     int64_t ldb, int64_t ncols, FieldP F) {
-  __shared__ uint32_t Lm[kTB][kTB + 1];
-  __shared__ uint32_t X[kTB][kStrip];
-  const int tid = threadIdx.x, tx = tid % kStrip, ty = tid / kStrip;
-  const int64_t c0 = (int64_t)blockIdx.x * kStrip;
-  for (int idx = tid; idx < r * r; idx += kTrsmThreads) {
-    const int i = idx / r, k = idx % r;
-    Lm[i][k] = (k < i) ? f_to_mont(L[(int64_t)i * ldl + k], F) : 0u;
+// ------------------------------------------------- diagonal-block inverses --
+//
+// One CTA inverts one diagonal block T of the triangle (rows and columns
+// [b tb, b tb + s), s <= tb <= kTB); the block is padded to kTB x kTB with
+// the identity.  An
+// upper block is inverted as the lower block T^T and stored transposed back
+// ((T^T)^{-1} = (T^{-1})^T).  Recursive doubling: with the inverses of the
+// two h x h diagonal blocks A, B of a 2h x 2h lower block [A 0; C B] known,
+// its inverse is [A^{-1} 0; -B^{-1} C A^{-1}  B^{-1}]; h = 1, 2, ..., kTB/2.
+// The result is written in Montgomery form (t R mod p) for the apply kernels.
+constexpr int kInvThreads = 256;
+
+template <bool kUpper, bool kUnit>
+__global__ void __launch_bounds__(kInvThreads)
+    k_tri_inv(const uint32_t* __restrict__ T, int64_t ldt, int r, int tb,
+              uint32_t* __restrict__ out, FieldP F, const uint32_t* __restrict__ inv_table) {
+  __shared__ uint32_t M[kTB][kTB + 1];
+  __shared__ uint32_t Y[kTB][kTB + 1];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int o = b * tb;
+  const int s = min(tb, r - o);
+  const bool big = F.p >= (1u << 26);  // 32 products of residues overflow 64 bits
+  // M = lower form of the block (T, or T^T for an upper block), identity padded
+  for (int idx = tid; idx < kTB * kTB; idx += kInvThreads) {
+    const int i = idx / kTB, k = idx % kTB;
+    uint32_t v = 0;
+    if (i < s && k < s && k <= i) v = kUpper ? T[(int64_t)(o + k) * ldt + o + i] : T[(int64_t)(o + i) * ldt + o + k];
+    if (i == k) v = (i >= s || kUnit) ? 1u : f_inv(v, F, inv_table);
+    M[i][k] = v;
   }
-  const bool colok = c0 + tx < ncols;
-  for (int i = ty; i < r; i += kTrsmThreads / kStrip)
-    X[i][tx] = colok ? B[(int64_t)i * ldb + c0 + tx] : 0u;
   __syncthreads();
-  for (int k = 0; k + 1 < r; ++k) {
-    const uint32_t xk = X[k][tx];
-    for (int i = ty; i < r; i += kTrsmThreads / kStrip)
-      if (i > k) X[i][tx] = f_sub(X[i][tx], f_mul_mont(Lm[i][k], xk, F), F);
+  for (int h = 1; h < kTB; h <<= 1) {
+    // Y = C A^{-1} for every pair; C = M[B rows, A cols] (original entries)
+    const int npairs = kTB / (2 * h), outs = npairs * h * h;
+    for (int idx = tid; idx < outs; idx += kInvThreads) {
+      const int q = idx / (h * h), rem = idx % (h * h), i = rem / h, j = rem % h;
+      const int a0 = 2 * q * h, b0 = a0 + h;
+      uint32_t v;
+      if (!big) {
+        uint64_t acc = 0;
+        for (int k = j; k < h; ++k) acc += (uint64_t)M[b0 + i][a0 + k] * M[a0 + k][a0 + j];
+        v = f_reduce64(acc, F);
+      } else {
+        v = 0;
+        for (int k = j; k < h; ++k) v = f_add(v, f_mul(M[b0 + i][a0 + k], M[a0 + k][a0 + j], F), F);
+      }
+      Y[b0 + i][a0 + j] = v;
+    }
     __syncthreads();
-  }
-  if (colok)
-    for (int i = ty; i < r; i += kTrsmThreads / kStrip) B[(int64_t)i * ldb + c0 + tx] = X[i][tx];
-}
-
-// B (nrows x r) <- B U^{-1}, U upper r x r, r <= kTB; one CTA per strip of
-// kStrip rows.  Threads own columns (tx) of B.
-__global__ void __launch_bounds__(kTrsmThreads)
-    k_trsm_ru_small(const uint32_t* __restrict__ U, int64_t ldu, int r, uint32_t* __restrict__ B,
-                    int64_t ldb, int64_t nrows, FieldP F, const uint32_t* __restrict__ inv_table) {
-  __shared__ uint32_t Um[kTB][kTB + 1];  // U' = D^{-1} U (unit upper), Montgomery form
-  __shared__ uint32_t dinv[kTB];
-  __shared__ uint32_t Y[kStrip][kTB + 1];
-  const int tid = threadIdx.x, tx = tid % kTB, ty = tid / kTB;
-  const int64_t r0 = (int64_t)blockIdx.x * kStrip;
-  if (tid < r) dinv[tid] = f_inv(U[(int64_t)tid * ldu + tid], F, inv_table);
-  for (int idx = tid; idx < kStrip * r; idx += kTrsmThreads) {
-    const int i = idx / r, j = idx % r;
-    Y[i][j] = (r0 + i < nrows) ? B[(r0 + i) * ldb + j] : 0u;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < r * r; idx += kTrsmThreads) {
-    const int j = idx / r, k = idx % r;
-    Um[j][k] = (k > j) ? f_to_mont(f_mul(U[(int64_t)j * ldu + k], dinv[j], F), F) : 0u;
-  }
-  __syncthreads();
-  // Y <- Y U'^{-1}: column k of Y loses Y[:, j] U'[j, k] for every j < k
-  for (int j = 0; j + 1 < r; ++j) {
-    if (tx > j && tx < r) {
-      const uint32_t u = Um[j][tx];
-      for (int i = ty; i < kStrip; i += kTrsmThreads / kTB)
-        Y[i][tx] = f_sub(Y[i][tx], f_mul_mont(u, Y[i][j], F), F);
+    // X = -B^{-1} Y into C's place
+    for (int idx = tid; idx < outs; idx += kInvThreads) {
+      const int q = idx / (h * h), rem = idx % (h * h), i = rem / h, j = rem % h;
+      const int a0 = 2 * q * h, b0 = a0 + h;
+      uint32_t v;
+      if (!big) {
+        uint64_t acc = 0;
+        for (int k = 0; k <= i; ++k) acc += (uint64_t)M[b0 + i][b0 + k] * Y[b0 + k][a0 + j];
+        v = f_reduce64(acc, F);
+      } else {
+        v = 0;
+        for (int k = 0; k <= i; ++k) v = f_add(v, f_mul(M[b0 + i][b0 + k], Y[b0 + k][a0 + j], F), F);
+      }
+      M[b0 + i][a0 + j] = f_sub(0u, v, F);
     }
     __syncthreads();
   }
-  // X = Y D^{-1}
-  for (int idx = tid; idx < kStrip * r; idx += kTrsmThreads) {
-    const int i = idx / r, j = idx % r;
-    if (r0 + i < nrows) B[(r0 + i) * ldb + j] = f_mul(Y[i][j], dinv[j], F);
+  uint32_t* dst = out + (size_t)b * kTB * kTB;
+  for (int idx = tid; idx < kTB * kTB; idx += kInvThreads) {
+    const int i = idx / kTB, k = idx % kTB;
+    const uint32_t v = kUpper ? M[k][i] : M[i][k];
+    dst[idx] = f_to_mont(v, F);
   }
 }
 
-// B (r x ncols) <- U^{-1} B, U upper r x r, r <= kTB.
-__global__ void __launch_bounds__(kTrsmThreads)
-    k_trsm_lu_small(const uint32_t* __restrict__ U, int64_t ldu, int r, uint32_t* __restrict__ B,
-                    int64_t ldb, int64_t ncols, FieldP F, const uint32_t* __restrict__ inv_table) {
-  __shared__ uint32_t Um[kTB][kTB + 1];  // U'' = D^{-1} U, Montgomery form
-  __shared__ uint32_t dinv[kTB];
-  __shared__ uint32_t X[kTB][kStrip];
-  const int tid = threadIdx.x, tx = tid % kStrip, ty = tid / kStrip;
+// ----------------------------------------------------------- apply kernels --
+//
+// X = Tinv Bblk (left; Bblk s x count) or X = Bblk Tinv (right; count x s),
+// in place, with Tinv (kTB x kTB, Montgomery form, zero outside the s x s
+// triangle) in shared memory.  Each CTA owns a strip of kStrip columns (left)
+// or rows (right) of the block, staged in shared memory before it is
+// overwritten.  An output is sum_k tinv_ik b_k: summed exactly in 64 bits and
+// reduced by one REDC (exact while the sum stays below p R: p < 2^26), else
+// one REDC per product.
+constexpr int kStrip = 32;
+constexpr int kApplyThreads = 256;
+
+template <bool kBig>
+__device__ __forceinline__ uint32_t mont_dot(const uint32_t* a, int sa, const uint32_t* x, int sx,
+                                             int len, const FieldP& F) {
+  if (!kBig) {
+    uint64_t s0 = 0, s1 = 0;
+    int k = 0;
+    for (; k + 1 < len; k += 2) {
+      s0 += (uint64_t)a[k * sa] * x[k * sx];
+      s1 += (uint64_t)a[(k + 1) * sa] * x[(k + 1) * sx];
+    }
+    if (k < len) s0 += (uint64_t)a[k * sa] * x[k * sx];
+    return F.is2 ? (uint32_t)((s0 + s1) & 1u) : f_redc(s0 + s1, F);
+  }
+  uint32_t acc = 0;
+  for (int k = 0; k < len; ++k) acc = f_add(acc, f_redc((uint64_t)a[k * sa] * x[k * sx], F), F);
+  return acc;
+}
+
+template <bool kBig>
+__global__ void __launch_bounds__(kApplyThreads)
+    k_tri_apply_left(const uint32_t* __restrict__ tinv, int s, uint32_t* __restrict__ B,
+                     int64_t ldb, int64_t count, FieldP F) {
+  __shared__ uint32_t Ti[kTB][kTB];
+  __shared__ uint32_t Xs[kTB][kStrip + 1];
+  const int tid = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * kStrip;
-  if (tid < r) dinv[tid] = f_inv(U[(int64_t)tid * ldu + tid], F, inv_table);
-  __syncthreads();
-  for (int idx = tid; idx < r * r; idx += kTrsmThreads) {
-    const int l = idx / r, k = idx % r;
-    Um[l][k] = (k > l) ? f_to_mont(f_mul(U[(int64_t)l * ldu + k], dinv[l], F), F) : 0u;
+  const int w = (int)(count - c0 < kStrip ? count - c0 : kStrip);
+  copy_g2s(&Ti[0][0], tinv, kTB * kTB, tid, kApplyThreads);
+  for (int idx0 = tid; idx0 < s * kStrip; idx0 += 8 * kApplyThreads) {
+    uint32_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = idx0 + q * kApplyThreads, k = idx / kStrip, j = idx % kStrip;
+      v[q] = (idx < s * kStrip && j < w) ? B[(int64_t)k * ldb + c0 + j] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = idx0 + q * kApplyThreads, k = idx / kStrip, j = idx % kStrip;
+      if (idx < s * kStrip) Xs[k][j] = v[q];
+    }
   }
-  const bool colok = c0 + tx < ncols;
-  for (int i = ty; i < r; i += kTrsmThreads / kStrip)
-    X[i][tx] = colok ? f_mul(B[(int64_t)i * ldb + c0 + tx], dinv[i], F) : 0u;
   __syncthreads();
-  for (int k = r - 1; k > 0; --k) {
-    const uint32_t xk = X[k][tx];
-    for (int l = ty; l < k; l += kTrsmThreads / kStrip)
-      X[l][tx] = f_sub(X[l][tx], f_mul_mont(Um[l][k], xk, F), F);
-    __syncthreads();
+  // thread: column j = tid % kStrip, rows i = tid / kStrip + 8 t
+  const int j = tid % kStrip;
+  uint32_t res[kTB / 8];
+#pragma unroll
+  for (int t = 0; t < kTB / 8; ++t) {
+    const int i = tid / kStrip + 8 * t;
+    res[t] = i < s ? mont_dot<kBig>(&Ti[i][0], 1, &Xs[0][j], kStrip + 1, s, F) : 0u;
   }
-  if (colok)
-    for (int i = ty; i < r; i += kTrsmThreads / kStrip) B[(int64_t)i * ldb + c0 + tx] = X[i][tx];
+  if (j < w) {
+#pragma unroll
+    for (int t = 0; t < kTB / 8; ++t) {
+      const int i = tid / kStrip + 8 * t;
+      if (i < s) B[(int64_t)i * ldb + c0 + j] = res[t];
+    }
+  }
+}
+
+template <bool kBig>
+__global__ void __launch_bounds__(kApplyThreads)
+    k_tri_apply_right(const uint32_t* __restrict__ tinv, int s, uint32_t* __restrict__ B,
+                      int64_t ldb, int64_t count, FieldP F) {
+  __shared__ uint32_t Ti[kTB][kTB];
+  __shared__ uint32_t Xs[kStrip][kTB + 1];
+  const int tid = threadIdx.x;
+  const int64_t t0 = (int64_t)blockIdx.x * kStrip;
+  const int h = (int)(count - t0 < kStrip ? count - t0 : kStrip);
+  copy_g2s(&Ti[0][0], tinv, kTB * kTB, tid, kApplyThreads);
+  for (int idx0 = tid; idx0 < kStrip * s; idx0 += 8 * kApplyThreads) {
+    uint32_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = idx0 + q * kApplyThreads, rr = idx / s, k = idx % s;
+      v[q] = (idx < kStrip * s && rr < h) ? B[(t0 + rr) * ldb + k] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = idx0 + q * kApplyThreads, rr = idx / s, k = idx % s;
+      if (idx < kStrip * s) Xs[rr][k] = v[q];
+    }
+  }
+  __syncthreads();
+  // thread: output column jj = tid % kTB, rows rr = tid / kTB + 4 t
+  const int jj = tid % kTB;
+  uint32_t res[kStrip / 4];
+#pragma unroll
+  for (int t = 0; t < kStrip / 4; ++t) {
+    const int rr = tid / kTB + 4 * t;
+    res[t] = jj < s ? mont_dot<kBig>(&Ti[0][jj], kTB, &Xs[rr][0], 1, s, F) : 0u;
+  }
+  __syncthreads();
+  if (jj < s) {
+#pragma unroll
+    for (int t = 0; t < kStrip / 4; ++t) Xs[tid / kTB + 4 * t][jj] = res[t];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < h * s; idx += kApplyThreads) {
+    const int rr = idx / s, k = idx % s;
+    B[(t0 + rr) * ldb + k] = Xs[rr][k];
+  }
+}
+
+enum TriKind { kLowerUnitLeft, kUpperLeft, kUpperRight };
+
+// Inverses of every diagonal block (size c->trsm_block) of the r x r
+// triangle into c->tri_inv.
+int invert_diag_blocks(pluq_ctx* c, TriKind kind, const uint32_t* T, int64_t ldt, int64_t r) {
+  const int tb = c->trsm_block;
+  const int64_t nb = cdiv(r, tb);
+  PLUQ_TRY(c->tri_inv.ensure(sizeof(uint32_t) * nb * kTB * kTB));
+  ProfScope ps(c, PC_TRSM, (double)nb * tb * tb * tb / 3.0, 8.0 * r * tb);
+  uint32_t* out = c->tri_inv.as<uint32_t>();
+  if (kind == kLowerUnitLeft)
+    k_tri_inv<false, true><<<(unsigned)nb, kInvThreads, 0, c->stream>>>(T, ldt, (int)r, tb, out,
+                                                                         c->F, inv_table_ptr(c));
+  else
+    k_tri_inv<true, false><<<(unsigned)nb, kInvThreads, 0, c->stream>>>(T, ldt, (int)r, tb, out,
+                                                                         c->F, inv_table_ptr(c));
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+// Diagonal block `blk` (size s <= kTB) applied to `count` columns (rows for
+// kUpperRight) of B.
+int apply_diag_block(pluq_ctx* c, TriKind kind, int64_t blk, int64_t s, uint32_t* B, int64_t ldb,
+                     int64_t count) {
+  if (s <= 0 || count <= 0) return PLUQ_OK;
+  ProfScope ps(c, PC_TRSM, (double)s * s * count, 8.0 * s * count);
+  const uint32_t* tinv = c->tri_inv.as<uint32_t>() + blk * kTB * kTB;
+  const unsigned g = (unsigned)cdiv(count, kStrip);
+  const bool big = c->F.p >= (1u << 26);
+  if (kind == kUpperRight) {
+    if (big)
+      k_tri_apply_right<true><<<g, kApplyThreads, 0, c->stream>>>(tinv, (int)s, B, ldb, count, c->F);
+    else
+      k_tri_apply_right<false><<<g, kApplyThreads, 0, c->stream>>>(tinv, (int)s, B, ldb, count, c->F);
+  } else {
+    if (big)
+      k_tri_apply_left<true><<<g, kApplyThreads, 0, c->stream>>>(tinv, (int)s, B, ldb, count, c->F);
+    else
+      k_tri_apply_left<false><<<g, kApplyThreads, 0, c->stream>>>(tinv, (int)s, B, ldb, count, c->F);
+  }
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
 }
 
 int64_t split_point(int64_t r, int64_t tb) {
@@ -117,56 +253,59 @@ int64_t split_point(int64_t r, int64_t tb) {
   return h;
 }
 
+// Recursive solves over the diagonal blocks [o, o + r) of the triangle (o a
+// multiple of the block size tb); the diagonal blocks were inverted
+// beforehand.
+int llu_rec(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t o, int64_t r, uint32_t* B,
+            int64_t ldb, int64_t ncols) {
+  const int64_t tb = c->trsm_block;
+  if (r <= tb) return apply_diag_block(c, kLowerUnitLeft, o / tb, r, B, ldb, ncols);
+  const int64_t r1 = split_point(r, tb);
+  PLUQ_TRY(llu_rec(c, L, ldl, o, r1, B, ldb, ncols));
+  PLUQ_TRY(fgemm_sub(c, r - r1, ncols, r1, L + r1 * ldl, ldl, B, ldb, B + r1 * ldb, ldb));
+  return llu_rec(c, L + r1 * ldl + r1, ldl, o + r1, r - r1, B + r1 * ldb, ldb, ncols);
+}
+
+int ru_rec(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t o, int64_t r, uint32_t* B,
+           int64_t ldb, int64_t nrows) {
+  const int64_t tb = c->trsm_block;
+  if (r <= tb) return apply_diag_block(c, kUpperRight, o / tb, r, B, ldb, nrows);
+  const int64_t r1 = split_point(r, tb);
+  PLUQ_TRY(ru_rec(c, U, ldu, o, r1, B, ldb, nrows));
+  PLUQ_TRY(fgemm_sub(c, nrows, r - r1, r1, B, ldb, U + r1, ldu, B + r1, ldb));
+  return ru_rec(c, U + r1 * ldu + r1, ldu, o + r1, r - r1, B + r1, ldb, nrows);
+}
+
+int lu_rec(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t o, int64_t r, uint32_t* B,
+           int64_t ldb, int64_t ncols) {
+  const int64_t tb = c->trsm_block;
+  if (r <= tb) return apply_diag_block(c, kUpperLeft, o / tb, r, B, ldb, ncols);
+  const int64_t r1 = split_point(r, tb);
+  // U = [U11 U12; 0 U22]: X2 = U22^{-1} B2, B1 -= U12 X2, X1 = U11^{-1} B1
+  PLUQ_TRY(lu_rec(c, U + r1 * ldu + r1, ldu, o + r1, r - r1, B + r1 * ldb, ldb, ncols));
+  PLUQ_TRY(fgemm_sub(c, r1, ncols, r - r1, U + r1, ldu, B + r1 * ldb, ldb, B, ldb));
+  return lu_rec(c, U, ldu, o, r1, B, ldb, ncols);
+}
+
 }  // namespace
 
 int trsm_left_lower_unit(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r, uint32_t* B,
                          int64_t ldb, int64_t ncols) {
   if (r <= 1 || ncols <= 0) return PLUQ_OK;  // a unit 1x1 triangle is the identity
-  const int64_t tb = c->trsm_block < kTB ? c->trsm_block : kTB;
-  if (r <= tb) {
-    ProfScope ps(c, PC_TRSM, (double)r * r * ncols, 8.0 * r * ncols);
-    k_trsm_llu_small<<<(unsigned)cdiv(ncols, kStrip), kTrsmThreads, 0, c->stream>>>(
-        L, ldl, (int)r, B, ldb, ncols, c->F);
-    PLUQ_CUDA(cudaGetLastError());
-    return PLUQ_OK;
-  }
-  const int64_t r1 = split_point(r, tb);
-  PLUQ_TRY(trsm_left_lower_unit(c, L, ldl, r1, B, ldb, ncols));
-  PLUQ_TRY(fgemm_sub(c, r - r1, ncols, r1, L + r1 * ldl, ldl, B, ldb, B + r1 * ldb, ldb));
-  return trsm_left_lower_unit(c, L + r1 * ldl + r1, ldl, r - r1, B + r1 * ldb, ldb, ncols);
+  PLUQ_TRY(invert_diag_blocks(c, kLowerUnitLeft, L, ldl, r));
+  return llu_rec(c, L, ldl, 0, r, B, ldb, ncols);
 }
 
 int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
                      int64_t ldb, int64_t nrows) {
   if (r <= 0 || nrows <= 0) return PLUQ_OK;
-  const int64_t tb = c->trsm_block < kTB ? c->trsm_block : kTB;
-  if (r <= tb) {
-    ProfScope ps(c, PC_TRSM, (double)r * r * nrows, 8.0 * r * nrows);
-    k_trsm_ru_small<<<(unsigned)cdiv(nrows, kStrip), kTrsmThreads, 0, c->stream>>>(
-        U, ldu, (int)r, B, ldb, nrows, c->F, inv_table_ptr(c));
-    PLUQ_CUDA(cudaGetLastError());
-    return PLUQ_OK;
-  }
-  const int64_t r1 = split_point(r, tb);
-  PLUQ_TRY(trsm_right_upper(c, U, ldu, r1, B, ldb, nrows));
-  PLUQ_TRY(fgemm_sub(c, nrows, r - r1, r1, B, ldb, U + r1, ldu, B + r1, ldb));
-  return trsm_right_upper(c, U + r1 * ldu + r1, ldu, r - r1, B + r1, ldb, nrows);
+  PLUQ_TRY(invert_diag_blocks(c, kUpperRight, U, ldu, r));
+  return ru_rec(c, U, ldu, 0, r, B, ldb, nrows);
 }
 
 int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
                     int64_t ldb, int64_t ncols) {
   if (r <= 0 || ncols <= 0) return PLUQ_OK;
-  const int64_t tb = c->trsm_block < kTB ? c->trsm_block : kTB;
-  if (r <= tb) {
-    ProfScope ps(c, PC_TRSM, (double)r * r * ncols, 8.0 * r * ncols);
-    k_trsm_lu_small<<<(unsigned)cdiv(ncols, kStrip), kTrsmThreads, 0, c->stream>>>(
-        U, ldu, (int)r, B, ldb, ncols, c->F, inv_table_ptr(c));
-    PLUQ_CUDA(cudaGetLastError());
-    return PLUQ_OK;
-  }
-  const int64_t r1 = split_point(r, tb);
-  // U = [U11 U12; 0 U22]: X2 = U22^{-1} B2, B1 -= U12 X2, X1 = U11^{-1} B1
-  PLUQ_TRY(trsm_left_upper(c, U + r1 * ldu + r1, ldu, r - r1, B + r1 * ldb, ldb, ncols));
-  PLUQ_TRY(fgemm_sub(c, r1, ncols, r - r1, U + r1, ldu, B + r1 * ldb, ldb, B, ldb));
-  return trsm_left_upper(c, U, ldu, r1, B, ldb, ncols);
+  PLUQ_TRY(invert_diag_blocks(c, kUpperLeft, U, ldu, r));
+  return lu_rec(c, U, ldu, 0, r, B, ldb, ncols);
 }
