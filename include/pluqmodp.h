@@ -191,6 +191,11 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        (each block is inverted, then applied as a product)
  *   PLUQ_OPT_CHAIN_ROWS  rows per CTA of wavefront leaves [0, 64]; 0 (default)
  *                        spreads the leaf over all SMs
+ *   PLUQ_OPT_FORK_DEPTH  recursion levels [0, 4] (default 2) at which the two
+ *                        independent calls on F and G run concurrently, each
+ *                        on its own stream, host thread and workspace with
+ *                        half the SMs for its leaves; 0 runs them in turn.
+ *                        Profiling (pluq_profile_enable) runs them in turn.
  * Errors: INVALID_ARG for an unknown option or a value out of range. */
 #define PLUQ_OPT_LEAF_DIM 1
 #define PLUQ_OPT_LEAF_KIND 2
@@ -198,6 +203,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_TILE_N 4
 #define PLUQ_OPT_TRSM_BLOCK 5
 #define PLUQ_OPT_CHAIN_ROWS 6
+#define PLUQ_OPT_FORK_DEPTH 7
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

@@ -176,12 +176,10 @@ __global__ void k_inv_table(uint32_t* table, uint32_t p) {
 
 int launch_base_pluq(pluq_ctx* c, uint32_t* A, int64_t lda, int m, int n, int32_t* perm_r,
                      int32_t* perm_c, int32_t* rank_out) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    PLUQ_CUDA(cudaFuncSetAttribute(k_base_pluq, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kBaseSmem));
-    attr_set = true;
-  }
+  // set once, thread-safely (function-local static initialisation)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_base_pluq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBaseSmem);
+  PLUQ_CUDA(attr);
   if (m > kBM || n > kBN || m <= 0 || n <= 0) return PLUQ_ERR_INVALID_ARG;
   ProfScope ps(c, PC_BASE, 0, 8.0 * m * n);
   k_base_pluq<<<1, kBaseThreads, kBaseSmem, c->stream>>>(A, lda, m, n, c->F, inv_table_ptr(c),

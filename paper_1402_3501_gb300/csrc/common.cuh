@@ -127,6 +127,8 @@ struct pluq_ctx {
   int device = 0;
   int sm_count = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;  // a child context's stream
+  cudaEvent_t fork_ev = nullptr;      // recorded before F and G start
   FieldP F{};
   int form = PLUQ_FORM_FP64;
   int bm = 128, bn = 128;  // base-case tile
@@ -158,6 +160,16 @@ struct pluq_ctx {
   DevBuf batch_scratch;    // per-CTA gather scratch of the batched kernel
   const void* batch_graph_key = nullptr;
   int32_t* host_small = nullptr;  // pinned host scalars
+  uint32_t limb_plan_p = 0;       // p of the cached limb fgemm plan
+  uint64_t limb_plan[4] = {0, 0, 0, 0};
+  // concurrent recursion (the independent calls on F and G): two child
+  // contexts, each with its own stream, workspace and host thread; they share
+  // the parent's index-vector slots and inverse table (disjoint ranges /
+  // read-only) and cooperative leaves in a child use at most its sm_count
+  int fork_depth = 2;             // levels of the recursion that run F and G concurrently
+  int lane_depth = 0;             // 0 for the user's context
+  pluq_ctx* parent = nullptr;
+  pluq_ctx* lane[2] = {nullptr, nullptr};
   // per-call statistics (host side)
   int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
   // device error flag (int) lives in small at offset 0

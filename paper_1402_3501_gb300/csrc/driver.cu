@@ -25,6 +25,7 @@
 // columns in their original relative order.
 #include <algorithm>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -191,6 +192,101 @@ dim3 grid2(int64_t rows, int64_t cols) {
   return dim3((unsigned)gx, (unsigned)gy, 1);
 }
 
+// ------------------------------------------------ concurrent F and G --
+//
+// The recursive calls on F and G read and write disjoint blocks of A and
+// disjoint ranges of the index vectors, and neither needs the other's result
+// (Sec. 2.3: F and G are factored independently before H is updated), so
+// they run on two child contexts at once: one host thread each, one stream
+// each, their own workspace, half the parent's SMs for cooperative leaves.
+constexpr int64_t kForkMinElems = 1024;
+
+void destroy_lane(pluq_ctx* l) {
+  if (!l) return;
+  destroy_lane(l->lane[0]);
+  destroy_lane(l->lane[1]);
+  l->perm_r = DevBuf{};  // views of the parent's buffers
+  l->perm_c = DevBuf{};
+  l->inv_table = DevBuf{};
+  l->scratch.release();
+  l->pack.release();
+  l->tmp_i.release();
+  l->tri_inv.release();
+  l->small.release();
+  l->leaf.release();
+  l->work.release();
+  for (cudaEvent_t e : l->prof.pool) cudaEventDestroy(e);
+  if (l->fork_ev) cudaEventDestroy(l->fork_ev);
+  if (l->host_small) cudaFreeHost(l->host_small);
+  if (l->own_stream) cudaStreamDestroy(l->own_stream);
+  delete l;
+}
+
+// Child context i of c, configured for a branch of m x n.
+int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
+  pluq_ctx*& l = c->lane[i];
+  if (!l) {
+    pluq_ctx* nl = new pluq_ctx();
+    nl->device = c->device;
+    nl->parent = c;
+    nl->lane_depth = c->lane_depth + 1;
+    if (cudaStreamCreateWithFlags(&nl->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&nl->host_small, 256) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_lane(nl);
+      return PLUQ_ERR_CUDA;
+    }
+    l = nl;
+  }
+  l->stream = l->own_stream;
+  l->sm_count = std::max(1, c->sm_count / 2);
+  l->F = c->F;
+  l->form = c->form;
+  l->bm = c->bm;
+  l->bn = c->bn;
+  l->trsm_block = c->trsm_block;
+  l->leaf_dim = c->leaf_dim;
+  l->leaf_kind = c->leaf_kind;
+  l->leaf_density = c->leaf_density;
+  l->chain_rows = c->chain_rows;
+  l->fork_depth = c->fork_depth;
+  l->mmax = c->mmax;
+  l->nmax = c->nmax;
+  l->limb_plan_p = c->limb_plan_p;
+  for (int k = 0; k < 4; ++k) l->limb_plan[k] = c->limb_plan[k];
+  l->perm_r = c->perm_r;
+  l->perm_c = c->perm_c;
+  l->inv_table = c->inv_table;
+  l->inv_table_p = c->inv_table_p;
+  l->prof.on = false;
+  for (int k = 0; k < PC_COUNT; ++k) l->launches[k] = 0;
+  l->n_base = l->n_nodes = l->n_gemm = 0;
+  // workspace for everything inside an m x n block, sized once (a growing
+  // allocation would synchronise the device under the other branch)
+  const int64_t mn = std::max<int64_t>(1, std::min(m, n));
+  PLUQ_TRY(l->small.ensure(256));
+  PLUQ_TRY(l->scratch.ensure(sizeof(uint32_t) * std::max<int64_t>(m * n, 1)));
+  PLUQ_TRY(l->tmp_i.ensure(sizeof(int32_t) * std::max(c->mmax, c->nmax)));
+  PLUQ_TRY(l->tri_inv.ensure(sizeof(uint32_t) * cdiv(mn, std::max(1, c->trsm_block)) * 64 * 64));
+  if (c->form == PLUQ_FORM_LIMB_F16) {
+    const int64_t kp = cdiv(mn / 2 + 64, 64) * 64;
+    const int64_t rows = cdiv(m, 128) * 128 + cdiv(n, 128) * 128;
+    PLUQ_TRY(l->pack.ensure(sizeof(uint16_t) * 4 * rows * kp + 4096));
+  }
+  const int64_t ld = std::min<int64_t>(std::max(c->leaf_dim, 1), std::max(m, n));
+  PLUQ_TRY(l->leaf.ensure(1024 + 16 * ld + 4 * ld * ld + 8 * (int64_t)c->sm_count * ld));
+  PLUQ_CUDA(cudaMemsetAsync(l->small.ptr, 0, 256, l->stream));
+  *out = l;
+  return PLUQ_OK;
+}
+
+void merge_lane_stats(pluq_ctx* c, const pluq_ctx* l) {
+  for (int k = 0; k < PC_COUNT; ++k) c->launches[k] += l->launches[k];
+  c->n_base += l->n_base;
+  c->n_nodes += l->n_nodes;
+  c->n_gemm += l->n_gemm;
+}
+
 struct Recursion {
   pluq_ctx* c;
   uint32_t* A;
@@ -203,6 +299,47 @@ struct Recursion {
   }
 
   int64_t split(int64_t x) { return x / 2; }
+
+  // Runs the recursive calls on F and G at once on the two child contexts
+  // (this thread takes G); returns after both streams have finished.
+  int fork_fg(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2, int64_t r1,
+              int d, int64_t* r2, int64_t* r3) {
+    pluq_ctx* lf = nullptr;
+    pluq_ctx* lg = nullptr;
+    PLUQ_TRY(get_lane(c, 0, m1 - r1, n2, &lf));
+    PLUQ_TRY(get_lane(c, 1, m2, n1 - r1, &lg));
+    if (!c->fork_ev) PLUQ_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    PLUQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+    PLUQ_CUDA(cudaStreamWaitEvent(lf->stream, c->fork_ev, 0));
+    PLUQ_CUDA(cudaStreamWaitEvent(lg->stream, c->fork_ev, 0));
+    auto finish = [](pluq_ctx* l, int st) {
+      // the branch's last kernels and its device error word
+      if (cudaMemcpyAsync(l->host_small, l->small.ptr, 32 * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, l->stream) != cudaSuccess ||
+          cudaStreamSynchronize(l->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return st != PLUQ_OK ? st : PLUQ_ERR_CUDA;
+      }
+      if (st != PLUQ_OK) return st;
+      return l->host_small[16] != 0 ? l->host_small[16] : PLUQ_OK;
+    };
+    int st_f = PLUQ_OK, st_g = PLUQ_OK;
+    std::thread tf([&] {
+      if (cudaSetDevice(lf->device) != cudaSuccess) {
+        st_f = PLUQ_ERR_CUDA;
+        return;
+      }
+      Recursion rf{lf, A, lda, lf->small.as<int32_t>() + 8};
+      st_f = finish(lf, rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2));
+    });
+    Recursion rg{lg, A, lda, lg->small.as<int32_t>() + 8};
+    st_g = finish(lg, rg.node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, r3));
+    tf.join();
+    merge_lane_stats(c, lf);
+    merge_lane_stats(c, lg);
+    c->leaf_density = lg->leaf_density;
+    return st_f != PLUQ_OK ? st_f : st_g;
+  }
 
   int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out) {
     int32_t* pr = PR(d) + R0;
@@ -264,18 +401,25 @@ struct Recursion {
                          X(R0, C0, m1, r1), lda));
     }
 
-    // F (rows r1..m1 of the top half, right columns)
-    int64_t r2 = 0;
-    PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2));
+    // F (rows r1..m1 of the top half, right columns) and G (bottom rows,
+    // columns r1..n1 of the left half): independent, concurrent when both
+    // are large; then the permutations each induces on the other blocks
+    int64_t r2 = 0, r3 = 0;
+    // (worth a thread when each block holds at least a quarter leaf)
+    const int64_t fork_min = std::max<int64_t>(kForkMinElems, lim_m * lim_n / 4);
+    const bool fork = c->lane_depth < c->fork_depth && !c->prof.on &&
+                      (m1 - r1) * n2 >= fork_min && m2 * (n1 - r1) >= fork_min;
+    if (fork) {
+      PLUQ_TRY(fork_fg(R0, C0, m1, n1, m2, n2, r1, d, &r2, &r3));
+    } else {
+      PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2));
+      PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3));
+    }
     PLUQ_TRY(launch_compose(c, pr + r1, cr + R0 + r1, m1 - r1));
     PLUQ_TRY(launch_compose(c, pc + n1, cc + C0 + n1, n2));
     PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
     PLUQ_TRY(permute_cols(c, X(R0, C0, 0, n1), lda, r1, n2, cc + C0 + n1));       // D
     PLUQ_TRY(permute_cols(c, X(R0, C0, m1, n1), lda, m2, n2, cc + C0 + n1));      // H
-
-    // G (bottom rows, columns r1..n1 of the left half)
-    int64_t r3 = 0;
-    PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3));
     PLUQ_TRY(launch_compose(c, pr + m1, cr + R0 + m1, m2));
     PLUQ_TRY(launch_compose(c, pc + r1, cc + C0 + r1, n1 - r1));
     PLUQ_TRY(permute_rows(c, X(R0, C0, m1, 0), lda, m2, r1, cr + R0 + m1));   // E
@@ -310,7 +454,7 @@ struct Recursion {
                           cc + C0 + n1 + r2));  // O
 
     // block-cyclic shifts
-    int32_t* tmp = PR(kMaxDepth - 1);  // spare row slot
+    int32_t* tmp = PR(kMaxDepth - 1) + R0;  // spare row slot (this block's range)
     {
       const int64_t a = r1 + r2, fr = m1 - r1 - r2, gr = r3 + r4;
       if (fr > 0 && gr > 0) {
@@ -325,7 +469,7 @@ struct Recursion {
       const int64_t gn = n1 - r1 - r3;
       const bool ident = (r2 == 0 || (r3 == 0 && gn == 0)) && (r4 == 0 || gn == 0);
       if (!ident) {
-        int32_t* tmpc = PC(kMaxDepth - 1);
+        int32_t* tmpc = PC(kMaxDepth - 1) + C0;
         const int64_t st[4] = {r3 + gn, 0, r3 + gn + r2, r3};
         const int64_t ln[4] = {r2, r3, r4, gn};
         const int64_t len = r3 + gn + r2 + r4;
@@ -490,6 +634,9 @@ int pluq_destroy(pluq_ctx* c) {
   if (!c) return PLUQ_OK;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  destroy_lane(c->lane[0]);
+  destroy_lane(c->lane[1]);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   c->scratch.release();
   c->pack.release();
   c->perm_r.release();
@@ -758,6 +905,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_CHAIN_ROWS:
       if (value < 0 || value > 64) return PLUQ_ERR_INVALID_ARG;
       c->chain_rows = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_FORK_DEPTH:
+      if (value < 0 || value > 4) return PLUQ_ERR_INVALID_ARG;
+      c->fork_depth = value;
       return PLUQ_OK;
     case PLUQ_OPT_TRSM_BLOCK:
       if (value < 1 || value > 64) return PLUQ_ERR_INVALID_ARG;

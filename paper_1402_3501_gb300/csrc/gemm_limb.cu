@@ -544,16 +544,18 @@ LimbPlan plan_for(uint32_t p) {
 
 using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
 
+EncodeTiled lookup_encode() {
+  void* ptr = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                       &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<EncodeTiled>(ptr);
+  return nullptr;
+}
+
 EncodeTiled get_encode() {
-  static EncodeTiled fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiled>(ptr);
-  }
+  static const EncodeTiled fn = lookup_encode();  // thread-safe one-time lookup
   return fn;
 }
 
@@ -574,12 +576,9 @@ template <int L>
 int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, const uint32_t* A,
              int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   using Cfg = LimbCfg<L>;
-  static bool attr = false;
-  if (!attr) {
-    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Cfg::kSmem));
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_fgemm_limb<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  PLUQ_CUDA(attr);
   constexpr int TN = Cfg::TN;
   const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, TN) * TN, Kp = cdiv(K, kTK) * kTK;
   if (L * Mp > INT32_MAX || L * Np > INT32_MAX || Kp > INT32_MAX) return PLUQ_ERR_INVALID_ARG;
@@ -618,12 +617,20 @@ int limb_form_supported(uint32_t p) { return plan_for(p).L > 0; }
 int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
                    const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
-  static uint32_t cached_p = 0;
-  static LimbPlan cached;
-  if (cached_p != c->F.p) {
-    cached = plan_for(c->F.p);
-    cached_p = c->F.p;
+  // the plan depends on p only; cached in the context (L, group, biases)
+  if (c->limb_plan_p != c->F.p) {
+    const LimbPlan pl = plan_for(c->F.p);
+    c->limb_plan[0] = (uint64_t)pl.L;
+    c->limb_plan[1] = (uint64_t)pl.group_kb;
+    c->limb_plan[2] = pl.bias;
+    c->limb_plan[3] = pl.bias_hi;
+    c->limb_plan_p = c->F.p;
   }
+  LimbPlan cached;
+  cached.L = (int)c->limb_plan[0];
+  cached.group_kb = (int)c->limb_plan[1];
+  cached.bias = c->limb_plan[2];
+  cached.bias_hi = c->limb_plan[3];
   if (cached.L == 1) return run_limb<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   if (cached.L == 2) return run_limb<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   if (cached.L == 3) return run_limb<3>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);

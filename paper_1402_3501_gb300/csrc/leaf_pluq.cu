@@ -293,7 +293,9 @@ int leaf_fits(pluq_ctx* c, int64_t m, int64_t n) {
 
 int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
                      int32_t* perm_c, int32_t* rank_out) {
-  static int max_smem_set = 0;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_leaf_pluq, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  PLUQ_CUDA(attr);
   // grid: at most one CTA per SM, at least ~8 owned rows per CTA
   int G = (m + 7) / 8;
   if (G > c->sm_count) G = c->sm_count;
@@ -304,11 +306,6 @@ int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_
     smem = leaf_smem(m, n, G);
   }
   if (smem > 220 * 1024) return PLUQ_ERR_INVALID_ARG;
-  if (max_smem_set < (int)smem) {
-    PLUQ_CUDA(cudaFuncSetAttribute(k_leaf_pluq, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   220 * 1024));
-    max_smem_set = 220 * 1024;
-  }
   // grid sync words and two candidate-row buffers of G rows each
   const size_t need = 256 + sizeof(uint32_t) * 2 * (size_t)G * n;
   PLUQ_TRY(c->leaf.ensure(need));
@@ -622,14 +619,12 @@ int chain_rows(pluq_ctx* c, int m, int n) {
 
 int launch_leaf_chain(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
                       int32_t* perm_c, int32_t* rank_out) {
-  static bool attr = false;
-  if (!attr) {
-    PLUQ_CUDA(cudaFuncSetAttribute(k_leaf_chain<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    PLUQ_CUDA(cudaFuncSetAttribute(k_leaf_chain<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr = true;
-  }
+  static const cudaError_t attr0 = cudaFuncSetAttribute(
+      k_leaf_chain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  static const cudaError_t attr1 = cudaFuncSetAttribute(
+      k_leaf_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  PLUQ_CUDA(attr0);
+  PLUQ_CUDA(attr1);
   int R = chain_rows(c, m, n);
   if (R < 1) return PLUQ_ERR_INVALID_ARG;
   const int G = (m + R - 1) / R;

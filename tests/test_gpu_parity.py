@@ -207,6 +207,23 @@ def test_pluq_large_primes(ctx, form, p, shape, frac):
             assert assert_parity(ctx, A, p, form) == r
 
 
+@pytest.mark.parametrize("fork_depth", [0, 1, 4])
+@pytest.mark.parametrize("leaf", [(96, 0), (96, 1), (0, 0)])
+@pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
+                                          (65521, (600, 450), 1.0)])
+def test_pluq_concurrent_branches(ctx, fork_depth, leaf, p, shape, frac):
+    """F and G factored concurrently on child contexts give the same result."""
+    m, n = shape
+    r = int(frac * min(m, n))
+    A = workloads.prescribed_rank_matrix(m, n, r, p, 9).A
+    ctx.set_option("fork_depth", fork_depth)
+    try:
+        with leaf_mode(ctx, leaf, tiles=(64, 64)):
+            assert assert_parity(ctx, A, p, "limb") == r
+    finally:
+        ctx.set_option("fork_depth", 2)
+
+
 @pytest.mark.parametrize("mode", [(0, (8, 8)), (0, (16, 8)), (0, (5, 13)), (0, (32, 32)),
                                   (0, (128, 64)), ((9, 0), (8, 8)), ((24, 0), (8, 8)),
                                   ((40, 0), (8, 8)), ((9, 1), (8, 8)), ((24, 1), (8, 8)),
