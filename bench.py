@@ -35,9 +35,9 @@ METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-e
 
 # DRAM traffic (read + write bytes) per launch of each kernel class from the
 # committed ncu captures (profiles/); None where no capture of the current kernel
-# exists.  The leaf figure was captured on a 1024x1024 leaf and scaled by the
-# element count to the 2048x2048 leaves of this workload.
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 4.36e6 * 4.0}
+# exists.  The leaf figure is the mean over three leaf launches of this workload
+# (blocks of about 1000 x 1000; writes stay in L2 until evicted).
+NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 3.49e6}
 
 
 def field_ops(m: int, n: int, r: int) -> float:
@@ -418,7 +418,7 @@ def bench_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["limb", "fp64", "auto"], default="limb")
