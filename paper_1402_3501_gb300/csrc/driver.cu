@@ -274,7 +274,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
     PLUQ_TRY(l->pack.ensure(sizeof(uint16_t) * 4 * rows * kp + 4096));
   }
   const int64_t ld = std::min<int64_t>(std::max(c->leaf_dim, 1), std::max(m, n));
-  PLUQ_TRY(l->leaf.ensure(1024 + 16 * ld + 4 * ld * ld + 8 * (int64_t)c->sm_count * ld));
+  PLUQ_TRY(l->leaf.ensure(4096 + 16 * ld + 4 * ld * ld + 8 * (int64_t)c->sm_count * (ld + 4)));
   PLUQ_CUDA(cudaMemsetAsync(l->small.ptr, 0, 256, l->stream));
   *out = l;
   return PLUQ_OK;

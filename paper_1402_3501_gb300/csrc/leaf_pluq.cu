@@ -5,10 +5,10 @@
 // CTA l mod G), so it is read from HBM once and written once.  Each step picks
 // the row-major first non-zero of the remaining Schur complement (the pivot
 // search of Sec. 4.1): every CTA proposes its first row with a non-zero
-// outside the pivot columns, publishing the row itself, and an atomicMin over
-// the row indices elects the pivot row; after one grid barrier every CTA
-// reads the elected row, finds its first non-zero column, and eliminates its
-// own rows below it.  Rows that reduce to zero are never visited again, so a
+// outside the pivot columns (tracked per row during elimination), publishing
+// the row with that column and the inverse of its entry there; after one grid
+// barrier every CTA elects the smallest proposed row index, reads that row and
+// eliminates its own rows below it.  Rows that reduce to zero are never visited again, so a
 // step costs one grid barrier per pivot, whatever the number of zero rows:
 // the cost follows the rank, which is what rank-deficient blocks need.
 //
@@ -28,11 +28,20 @@ constexpr int kLeafThreads = 512;
 constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s
 
+// Grid barrier words and the candidate election of the barrier leaf.  Each
+// CTA writes its candidate (global row index, INT_MAX for none) to its own
+// slot cand[step & 1][cta] before arriving; after the barrier every CTA
+// reduces the G slots itself (one round of parallel loads) instead of all
+// CTAs contending for one atomicMin word.  Two slot arrays by step parity: a
+// CTA rewrites cand[s & 1] at the end of step s + 1, after every CTA passed
+// the barrier of step s + 1 and so finished reading step s's slots.
+constexpr int kLeafMaxCtas = 256;
 struct LeafSync {
   unsigned count;
   unsigned gen;
-  int best[3];
   int abort;
+  int pad[29];
+  int cand[2][kLeafMaxCtas];
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -106,24 +115,30 @@ __device__ void compact_unflagged(const int32_t* flag, int count, int32_t* out, 
   __syncthreads();
 }
 
+// Words per candidate slot: the row, its live column and the Montgomery
+// inverse of its entry there, padded to 16 bytes.
+__host__ __device__ inline int leaf_slot(int n) { return (n + 2 + 3) & ~3; }
+
 __global__ void __launch_bounds__(kLeafThreads, 1)
     k_leaf_pluq(uint32_t* __restrict__ X, int64_t ldx, int m, int n, FieldP F,
                 const uint32_t* __restrict__ inv_table, int32_t* __restrict__ perm_r,
                 int32_t* __restrict__ perm_c, int32_t* __restrict__ rank_out, LeafSync* sync,
                 uint32_t* __restrict__ candbuf, int* __restrict__ err) {
   extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ uint32_t s_hdr[2];  // elected pivot column and Montgomery inverse
   const unsigned G = gridDim.x;
   const int cta = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rown = (m + G - 1) / G;  // owned-row capacity
   const int mn = min(m, n);
+  const int slot = leaf_slot(n);
   uint32_t* W = sm;                                             // [rown][n]
   uint32_t* piv = W + (size_t)rown * n;                         // [n] elected row
   int32_t* ispiv = reinterpret_cast<int32_t*>(piv + n);         // [n]
   int32_t* prow = ispiv + n;                                    // [mn]
   int32_t* pcol = prow + mn;                                    // [mn]
-  int32_t* rowflag = pcol + mn;                                 // [rown]
-  int32_t* red = rowflag + rown;                                // [64]
+  int32_t* fcol = pcol + mn;                                    // [rown] first live column
+  int32_t* red = fcol + rown;                                   // [64]
   int32_t* rowpos = red + 64;                                   // [m]
   int32_t* rowinv = rowpos + m;                                 // [m]
   int32_t* isprow = rowinv + m;                                 // [m]
@@ -136,105 +151,106 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
   copy_rows_g2s(W, X + (int64_t)cta * ldx, ldx * (int64_t)G, owned, n, warp, lane, kLeafWarps);
   for (int j = tid; j < n; j += kLeafThreads) ispiv[j] = 0;
   __syncthreads();
-
-  unsigned gen = 0;
-  // first candidate: first owned row with a non-zero
+  // fcol[lr]: first non-zero column of owned row lr outside the pivot columns
+  // (INT_MAX: none left, or the row became a pivot row), refreshed by the
+  // warp that eliminates the row
   for (int lr = warp; lr < owned; lr += kLeafWarps) {
-    bool nz = false;
-    for (int j = lane; j < n; j += 32) nz |= W[(size_t)lr * n + j] != 0u;
-    nz = __any_sync(0xffffffffu, nz);
-    if (lane == 0) rowflag[lr] = nz ? 1 : 0;
-  }
-  __syncthreads();
-  {
-    int first = -1;
-    for (int lr = 0; lr < owned; ++lr)
-      if (rowflag[lr]) {
-        first = lr;
+    const uint32_t* Wl = W + (size_t)lr * n;
+    int jl = INT_MAX;
+    for (int j = lane; j < n; j += 32)
+      if (Wl[j] != 0u) {
+        jl = j;
         break;
       }
-    if (first >= 0) {
-      uint32_t* dst = candbuf + (size_t)cta * n;
-      for (int j = tid; j < n; j += kLeafThreads) dst[j] = W[(size_t)first * n + j];
-      if (tid == 0) atomicMin(&sync->best[0], first * (int)G + cta);
-    }
+    jl = __reduce_min_sync(0xffffffffu, jl);
+    if (lane == 0) fcol[lr] = jl;
   }
+  __syncthreads();
+
+  // this CTA's candidate for the next step: its first owned row with a live
+  // column, published with that column and the inverse of its entry there
+  auto publish = [&](int buf) {
+    int first = INT_MAX;
+    for (int b0 = 0; b0 < owned; b0 += 32) {
+      const int lr = b0 + lane;
+      const unsigned hit = __ballot_sync(0xffffffffu, lr < owned && fcol[lr] != INT_MAX);
+      if (hit) {
+        first = b0 + __ffs(hit) - 1;
+        break;
+      }
+    }
+    if (first != INT_MAX) {
+      uint32_t* dst = candbuf + ((size_t)buf * G + cta) * slot;
+      const uint32_t* src = W + (size_t)first * n;
+      for (int j = tid; j < n; j += kLeafThreads) dst[j] = src[j];
+      if (tid == 0) {
+        const int j0 = fcol[first];
+        dst[n] = (uint32_t)j0;
+        dst[n + 1] = f_to_mont(f_inv(src[j0], F, inv_table), F);
+      }
+    }
+    if (tid == 0) sync->cand[buf][cta] = first == INT_MAX ? INT_MAX : first * (int)G + cta;
+  };
+  // elected row of step k: smallest candidate over the G slots (all threads)
+  auto elect = [&](int buf) {
+    int v = tid < (int)G ? __ldcg(&sync->cand[buf][tid]) : INT_MAX;
+    v = __reduce_min_sync(0xffffffffu, v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int best = INT_MAX;
+    for (int w = 0; w < kLeafWarps; ++w) best = min(best, red[w]);
+    return best;
+  };
+
+  unsigned gen = 0;
+  publish(0);
   bool ok = grid_barrier(sync, G, gen, err);
 
   int r = 0;
   for (int k = 0; ok; ++k) {
-    const int istar = ld_volatile_i(&sync->best[k % 3]);
-    if (cta == 0 && tid == 0) sync->best[(k + 2) % 3] = INT_MAX;
+    const int istar = elect(k & 1);
     if (istar == INT_MAX || r >= mn) break;
     const int winner = istar % (int)G;
-    const uint32_t* crow = candbuf + ((size_t)(k & 1) * G + winner) * n;
+    const uint32_t* crow = candbuf + ((size_t)(k & 1) * G + winner) * slot;
     // L2 loads: the buffer is rewritten every other step by other SMs
     for (int j = tid; j < n; j += kLeafThreads) piv[j] = __ldcg(crow + j);
+    if (tid < 2) s_hdr[tid] = __ldcg(crow + n + tid);
     __syncthreads();
-    // pivot column: first non-zero of the elected row outside the pivots
-    int jl = INT_MAX;
-    for (int j = tid; j < n; j += kLeafThreads)
-      if (!ispiv[j] && piv[j] != 0u) {
-        jl = j;
-        break;
+    const int j0 = (int)s_hdr[0];
+    const uint32_t inv_m = s_hdr[1];
+    // eliminate owned rows below the pivot row; the pivot row leaves the race
+    for (int lr = warp; lr < owned; lr += kLeafWarps) {
+      const int l = lr * (int)G + cta;
+      if (l == istar) {
+        if (lane == 0) fcol[lr] = INT_MAX;
+        continue;
       }
-    for (int o = 16; o > 0; o >>= 1) jl = min(jl, __shfl_xor_sync(0xffffffffu, jl, o));
-    if (lane == 0) red[warp] = jl;
-    __syncthreads();
-    int j0 = INT_MAX;
-    for (int w = 0; w < kLeafWarps; ++w) j0 = min(j0, red[w]);
-    if (j0 == INT_MAX) {  // unreachable: the elected row has a non-zero off the pivots
-      if (tid == 0) atomicExch(err, PLUQ_ERR_INVALID_ARG);
-      break;
+      if (l < istar) continue;  // zero or pivot rows
+      uint32_t* Wl = W + (size_t)lr * n;
+      const uint32_t wl = Wl[j0];
+      if (wl == 0u) continue;  // unchanged; its first live column is not j0
+      const uint32_t cmul = f_mul_mont(inv_m, wl, F);
+      const uint32_t cm = f_to_mont(cmul, F);
+      int jl = INT_MAX;
+      for (int j = lane; j < n; j += 32) {
+        if (j == j0 || ispiv[j]) continue;
+        const uint32_t nv = f_sub(Wl[j], f_mul_mont(cm, piv[j], F), F);
+        Wl[j] = nv;
+        if (nv != 0u && jl == INT_MAX) jl = j;
+      }
+      jl = __reduce_min_sync(0xffffffffu, jl);
+      if (lane == 0) {
+        Wl[j0] = cmul;
+        fcol[lr] = jl;
+      }
     }
-    const uint32_t inv = f_inv(piv[j0], F, inv_table);
-    const uint32_t inv_m = f_to_mont(inv, F);
-    __syncthreads();
     if (tid == 0) {
       prow[r] = istar;
       pcol[r] = j0;
       ispiv[j0] = 1;
     }
     __syncthreads();
-    // eliminate owned rows below the pivot row
-    for (int lr = warp; lr < owned; lr += kLeafWarps) {
-      const int l = lr * (int)G + cta;
-      uint32_t* Wl = W + (size_t)lr * n;
-      bool nz = false;
-      if (l > istar) {
-        const uint32_t wl = Wl[j0];
-        __syncwarp();
-        if (wl != 0u) {
-          const uint32_t cmul = f_mul_mont(inv_m, wl, F);
-          const uint32_t cm = f_to_mont(cmul, F);
-          for (int j = lane; j < n; j += 32) {
-            if (j == j0) {
-              Wl[j] = cmul;
-            } else if (!ispiv[j]) {
-              const uint32_t nv = f_sub(Wl[j], f_mul_mont(cm, piv[j], F), F);
-              Wl[j] = nv;
-              nz |= nv != 0u;
-            }
-          }
-        } else {
-          for (int j = lane; j < n; j += 32) nz |= !ispiv[j] && Wl[j] != 0u;
-        }
-      }
-      nz = __any_sync(0xffffffffu, nz);
-      if (lane == 0) rowflag[lr] = nz ? 1 : 0;
-    }
-    __syncthreads();
-    int first = -1;
-    for (int lr = 0; lr < owned; ++lr)
-      if (rowflag[lr]) {
-        first = lr;
-        break;
-      }
-    if (first >= 0) {
-      uint32_t* dst = candbuf + ((size_t)((k + 1) & 1) * G + cta) * n;
-      for (int j = tid; j < n; j += kLeafThreads) dst[j] = W[(size_t)first * n + j];
-      if (tid == 0) atomicMin(&sync->best[(k + 1) % 3], first * (int)G + cta);
-    }
+    publish((k + 1) & 1);
     ++r;
     ok = grid_barrier(sync, G, gen, err);
   }
@@ -268,10 +284,12 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
 }
 
 __global__ void k_leaf_init(LeafSync* s) {
-  s->count = 0u;
-  s->gen = 0u;
-  s->best[0] = s->best[1] = s->best[2] = INT_MAX;
-  s->abort = 0;
+  if (threadIdx.x == 0) {
+    s->count = 0u;
+    s->gen = 0u;
+    s->abort = 0;
+  }
+  for (int i = threadIdx.x; i < kLeafMaxCtas; i += blockDim.x) s->cand[0][i] = s->cand[1][i] = INT_MAX;
 }
 
 size_t leaf_smem(int m, int n, int G) {
@@ -306,14 +324,16 @@ int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_
     smem = leaf_smem(m, n, G);
   }
   if (smem > 220 * 1024) return PLUQ_ERR_INVALID_ARG;
-  // grid sync words and two candidate-row buffers of G rows each
-  const size_t need = 256 + sizeof(uint32_t) * 2 * (size_t)G * n;
+  // barrier words, election slots and two candidate-row buffers of G rows each
+  if (G > kLeafMaxCtas || G > kLeafThreads) return PLUQ_ERR_INVALID_ARG;
+  const size_t head = (sizeof(LeafSync) + 255) / 256 * 256;
+  const size_t need = head + sizeof(uint32_t) * 2 * (size_t)G * leaf_slot(n);
   PLUQ_TRY(c->leaf.ensure(need));
   LeafSync* sync = c->leaf.as<LeafSync>();
-  uint32_t* candbuf = reinterpret_cast<uint32_t*>(c->leaf.as<char>() + 256);
+  uint32_t* candbuf = reinterpret_cast<uint32_t*>(c->leaf.as<char>() + head);
   {
     ProfScope pi(c, PC_INDEX);
-    k_leaf_init<<<1, 1, 0, c->stream>>>(sync);
+    k_leaf_init<<<1, 256, 0, c->stream>>>(sync);
   }
   int* err = c->small.as<int>() + 16;
   const uint32_t* tab = inv_table_ptr(c);
