@@ -301,7 +301,11 @@ def bench_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     form = args.form
 
+    # schedule chosen by the library's autotuner on this matrix (untimed), then
     # warm-up (not timed) and bit-exact validation against the construction
+    schedule = None
+    if not args.no_autotune:
+        schedule = ctx.autotune(A0, p, form=form, budget_ms=args.tune_budget_ms)
     for _ in range(args.warmup):
         A.copy_(A0)
         res = pq.pluq_modp(A, p, form=form, ctx=ctx)
@@ -418,6 +422,7 @@ def bench_ours(args, world, rank, local):
             "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "p": p, "form": form,
                        "l2": "inputs (268 MB) larger than L2 (129 MB), no flush",
                        "step": "restore input (D2D copy) + pluq_modp",
+                       "schedule": schedule or "default (leaf 1024, per-leaf kind, fork depth 2)",
                        "parallelism": f"replicas x{world}"},
             "bitexact": exact,
             "fgemm_dtype": "f16 digits, f32 accumulate" if form != "fp64" else "f64",
@@ -448,6 +453,9 @@ def main():
     ap.add_argument("--form", choices=["limb", "fp64", "auto"], default="limb")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default schedule instead of the autotuned one")
+    ap.add_argument("--tune-budget-ms", type=float, default=15000.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS),
                     help="matrix to factor (the default is the measured workload; the "
                          "others serve as small profiling cases)")

@@ -106,6 +106,21 @@ int echelon_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_t
                  int64_t lda, uint32_t* R, int64_t ldr, int64_t* rank_dev, int32_t* crp,
                  int form, void* stream);
 
+/* Reduced column echelon form of A over GF(p): E = RREF(A^T)^T, the echelon
+ * form by columns that the paper also names (Sec. 4.1): pivots equal to 1,
+ * zeros to their left, columns ordered by pivot row, the pivot rows being the
+ * row rank profile.  Computed as the RREF of the transpose (one transpose
+ * pass into the workspace, then as echelon_modp).
+ *   A        device, m x n, lda >= n; not modified.
+ *   C        device, m x min(m,n), ldc >= min(m,n); receives the m x r form
+ *            in its first r columns (columns r.. are left untouched).
+ *   rank_dev device int64 scalar (may be NULL).
+ *   rrp      device int32, length >= min(m,n) (may be NULL): pivot rows.
+ * Errors: as pluq_modp. */
+int column_echelon_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_t* A,
+                        int64_t lda, uint32_t* C, int64_t ldc, int64_t* rank_dev, int32_t* rrp,
+                        int form, void* stream);
+
 /* Rank and both rank profiles of A over GF(p) (Sec. 4.1), A unmodified.
  *   rank_dev       device int64 scalar (may be NULL).
  *   rrp, crp       device int32, length >= min(m,n) (may be NULL).
@@ -196,6 +211,9 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        on its own stream, host thread and workspace with
  *                        half the SMs for its leaves; 0 runs them in turn.
  *                        Profiling (pluq_profile_enable) runs them in turn.
+ *   PLUQ_OPT_USE_TUNED   1 (default): factorizations whose (p, m, n, form)
+ *                        was autotuned use the tuned schedule in place of
+ *                        LEAF_DIM, LEAF_KIND and FORK_DEPTH; 0: ignore it.
  * Errors: INVALID_ARG for an unknown option or a value out of range. */
 #define PLUQ_OPT_LEAF_DIM 1
 #define PLUQ_OPT_LEAF_KIND 2
@@ -204,6 +222,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_TRSM_BLOCK 5
 #define PLUQ_OPT_CHAIN_ROWS 6
 #define PLUQ_OPT_FORK_DEPTH 7
+#define PLUQ_OPT_USE_TUNED 8
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a
@@ -215,6 +234,23 @@ int pluq_set_leaf(pluq_ctx* ctx, int leaf_dim);
 /* Counters of the last call: base-case launches, internal recursion nodes,
  * fgemm calls. */
 int pluq_last_stats(pluq_ctx* ctx, int64_t* n_base, int64_t* n_nodes, int64_t* n_gemm);
+
+/* Autotuner of the recursion schedule (no counterpart in the paper, which tunes
+ * by hand for one machine): times pluq_modp on copies of A (device, m x n, row
+ * stride lda, read only) under candidate schedules - leaf cut-off 1024, 512,
+ * 2048 crossed with leaf kind per-leaf choice, barrier, wavefront (fork depth
+ * 2), then fork depth 0, 1, 3 for the best - one warm run and the best of two
+ * timed runs each, stopping once budget_ms (0: 10 s) is spent after at least
+ * one schedule.  The fastest is stored in the context for (p, m, n, form) and
+ * applied by later pluq_modp / echelon_modp / rank_profile_modp calls of that
+ * shape (PLUQ_OPT_USE_TUNED); a new call for the shape replaces it.  The
+ * timings depend on A's rank structure, so tune on a representative matrix.
+ * chosen (host, may be NULL): leaf cut-off, leaf kind, fork depth; best_ms
+ * (host, may be NULL): its time.  Synchronises the stream.
+ * Errors: as pluq_modp, NO_WORKSPACE (two m x n copies). */
+int pluq_autotune(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_t* A,
+                  int64_t lda, int form, void* stream, double budget_ms, int32_t* chosen,
+                  double* best_ms);
 
 /* Per-kernel-class timers.  pluq_profile_enable(ctx, 1) resets the counters
  * and brackets every later kernel launch with CUDA events on the call's

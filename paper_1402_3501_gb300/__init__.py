@@ -7,12 +7,12 @@ holds the CUDA sources (csrc/), the in-tree build (build.py) and the Python
 binding (binding.py).
 """
 from .binding import (BatchPlan, FORM_AUTO, FORM_FP64, FORM_LIMB_F16, Context, PluqError, PLUQResult,
-                      default_context, echelon_modp, fgemm_modp, fgemm_modp_noalloc, load, pluq_modp,
-                      pluq_modp_batched, rank_profile_modp)
+                      column_echelon_modp, default_context, echelon_modp, fgemm_modp,
+                      fgemm_modp_noalloc, load, pluq_modp, pluq_modp_batched, rank_profile_modp)
 
 __all__ = [
     "BatchPlan",
     "FORM_AUTO", "FORM_FP64", "FORM_LIMB_F16", "Context", "PluqError", "PLUQResult",
-    "default_context", "echelon_modp", "fgemm_modp", "fgemm_modp_noalloc", "load", "pluq_modp", "pluq_modp_batched",
-    "rank_profile_modp",
+    "column_echelon_modp", "default_context", "echelon_modp", "fgemm_modp", "fgemm_modp_noalloc",
+    "load", "pluq_modp", "pluq_modp_batched", "rank_profile_modp",
 ]

@@ -35,7 +35,7 @@ SYMBOLS = [
     "pluq_create", "pluq_destroy", "pluq_modp", "echelon_modp", "rank_profile_modp",
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
     "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
-    "fgemm_modp_noalloc", "pluq_set_option",
+    "fgemm_modp_noalloc", "pluq_set_option", "pluq_autotune", "column_echelon_modp",
 ]
 
 
@@ -60,6 +60,7 @@ def load():
         "pluq_destroy": [vp],
         "pluq_modp": [vp, u32, i64, i64, vp, i64, vp, vp, vp, vp, vp, i32, vp],
         "echelon_modp": [vp, u32, i64, i64, vp, i64, vp, i64, vp, vp, i32, vp],
+        "column_echelon_modp": [vp, u32, i64, i64, vp, i64, vp, i64, vp, vp, i32, vp],
         "rank_profile_modp": [vp, u32, i64, i64, vp, i64, vp, vp, vp, vp, i32, vp],
         "fgemm_modp": [vp, u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp],
         "pluq_modp_batched": [vp, u32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp],
@@ -72,6 +73,7 @@ def load():
         "pluq_set_option": [vp, i32, i32],
         "fgemm_modp_noalloc": [u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp],
         "pluq_profile_read": [vp, i32, vp, vp, vp, vp, vp],
+        "pluq_autotune": [vp, u32, i64, i64, vp, i64, i32, vp, ctypes.c_double, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -139,7 +141,7 @@ class Context:
             pass
 
     OPTIONS = {"leaf_dim": 1, "leaf_kind": 2, "tile_m": 3, "tile_n": 4, "trsm_block": 5,
-               "chain_rows": 6, "fork_depth": 7}
+               "chain_rows": 6, "fork_depth": 7, "use_tuned": 8}
 
     def set_option(self, name: str, value: int):
         """Set a recursion option (see PLUQ_OPT_* in include/pluqmodp.h)."""
@@ -171,6 +173,21 @@ class Context:
             out[name] = {"launches": nl.value, "ms": ms.value, "flops": fl.value,
                          "bytes": by.value, "tensor_flops": tf.value}
         return out
+
+    LEAF_KINDS = {0: "barrier", 1: "wavefront", 2: "per-leaf"}
+
+    def autotune(self, A: torch.Tensor, p: int, form="limb", budget_ms: float = 0.0,
+                 stream=None) -> dict:
+        """Time candidate recursion schedules on copies of A and keep the fastest for
+        A's (p, shape, form) in this context (pluq_autotune); A is not modified."""
+        m, n, ld = _matrix_args(A)
+        chosen = (ctypes.c_int32 * 3)()
+        best = ctypes.c_double()
+        _check(load().pluq_autotune(self.handle, p, m, n, ctypes.c_void_p(A.data_ptr()), ld,
+                                    _form(form), _stream_handle(stream), float(budget_ms), chosen,
+                                    ctypes.byref(best)), "pluq_autotune")
+        return {"leaf_dim": chosen[0], "leaf_kind": self.LEAF_KINDS.get(chosen[1], chosen[1]),
+                "fork_depth": chosen[2], "ms": best.value}
 
     def last_stats(self) -> dict:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -233,6 +250,22 @@ def echelon_modp(A: torch.Tensor, p: int, form="auto", ctx: Context | None = Non
     _check(st, "echelon_modp")
     r = last_rank(ctx)
     return r, R[:r, :n], crp[:r]
+
+
+def column_echelon_modp(A: torch.Tensor, p: int, form="auto", ctx: Context | None = None,
+                        stream=None):
+    """Reduced column echelon form RREF(A^T)^T: returns (rank, E (m x r int32), rrp)."""
+    ctx = ctx or default_context(A.device.index)
+    m, n, lda = _matrix_args(A)
+    dev = A.device
+    rmax = max(min(m, n), 1)
+    E = torch.zeros((max(m, 1), rmax), dtype=torch.int32, device=dev)
+    rrp = torch.empty(rmax, dtype=torch.int32, device=dev)
+    st = load().column_echelon_modp(ctx.handle, p, m, n, _dev_ptr(A), lda, _dev_ptr(E), rmax,
+                                    None, _dev_ptr(rrp), _form(form), _stream_handle(stream))
+    _check(st, "column_echelon_modp")
+    r = last_rank(ctx)
+    return r, E[:m, :r], rrp[:r]
 
 
 def rank_profile_modp(A: torch.Tensor, p: int, form="auto", ctx: Context | None = None,

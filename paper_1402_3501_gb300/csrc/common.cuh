@@ -170,6 +170,18 @@ struct pluq_ctx {
   int lane_depth = 0;             // 0 for the user's context
   pluq_ctx* parent = nullptr;
   pluq_ctx* lane[2] = {nullptr, nullptr};
+  // schedules chosen by pluq_autotune, per (p, m, n, form); applied by every
+  // factorization of a matching shape unless use_tuned is 0
+  struct Tuned {
+    uint32_t p;
+    int64_t m, n;
+    int form, leaf_dim, leaf_kind, fork_depth;
+    double ms;
+  };
+  std::vector<Tuned> tuned;
+  int use_tuned = 1;
+  bool tuning = false;            // inside pluq_autotune: candidates set explicitly
+  DevBuf tune_src, tune_dst;      // the caller's matrix and a trial copy
   // per-call statistics (host side)
   int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
   // device error flag (int) lives in small at offset 0

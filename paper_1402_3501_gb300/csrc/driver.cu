@@ -24,6 +24,7 @@
 // rank profile matrix because every call keeps its non-pivot rows and
 // columns in their original relative order.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -167,17 +168,36 @@ __global__ void k_invert_perm(const int32_t* __restrict__ Q, int64_t n, int32_t*
 }
 
 // RREF row t = pivot ord[t] (ord[t] = qinv[crp[t]]) of X = [I | U1^{-1} U2]
-// in the Q frame, scattered back to the original column order.
+// in the Q frame, scattered back to the original column order: entry (t, col)
+// goes to R[t * rs + col * cs] (rs = ldr, cs = 1 for the row form; rs = 1,
+// cs = ldc for its transpose, the column echelon form of the transposed input).
 __global__ void k_rref_scatter(const uint32_t* __restrict__ W, int64_t ldw, int64_t r, int64_t n,
                                const int32_t* __restrict__ qinv, const int32_t* __restrict__ crp,
-                               uint32_t* __restrict__ R, int64_t ldr) {
+                               uint32_t* __restrict__ R, int64_t rs, int64_t cs) {
   for (int64_t t = blockIdx.y; t < r; t += gridDim.y) {
     const int32_t k = qinv[crp[t]];
     for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < n;
          col += (int64_t)gridDim.x * blockDim.x) {
       const int32_t j = qinv[col];
-      R[t * ldr + col] = j < r ? (j == k ? 1u : 0u) : W[(int64_t)k * ldw + j];
+      R[t * rs + col * cs] = j < r ? (j == k ? 1u : 0u) : W[(int64_t)k * ldw + j];
     }
+  }
+}
+
+// dst (cols x rows, ldd) = src (rows x cols, lds)^T through 32 x 32 tiles.
+__global__ void k_transpose(uint32_t* __restrict__ dst, int64_t ldd,
+                            const uint32_t* __restrict__ src, int64_t lds, int64_t rows,
+                            int64_t cols) {
+  __shared__ uint32_t tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0u;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[c * ldd + r] = tile[threadIdx.x][i];
   }
 }
 
@@ -375,8 +395,14 @@ struct Recursion {
     }
     if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
     c->n_nodes++;
-    const int64_t lim_m = c->leaf_dim > 0 ? c->leaf_dim : c->bm;
-    const int64_t lim_n = c->leaf_dim > 0 ? c->leaf_dim : c->bn;
+    int64_t lim_m = c->leaf_dim > 0 ? c->leaf_dim : c->bm;
+    int64_t lim_n = c->leaf_dim > 0 ? c->leaf_dim : c->bn;
+    if (m <= lim_m && n <= lim_n) {
+      // within the cut-off but no leaf kernel takes the block (its shared
+      // memory needs more SMs than this context has): split it all the same
+      lim_m = std::max<int64_t>(1, m / 2);
+      lim_n = std::max<int64_t>(1, n / 2);
+    }
     const int64_t m1 = m > lim_m ? split(m) : m;
     const int64_t n1 = n > lim_n ? split(n) : n;
     const int64_t m2 = m - m1, n2 = n - n1;
@@ -500,7 +526,31 @@ int prepare(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, int form, void* strea
 }
 
 // Factor A in place; leaves P = PR(0), Q = PC(0) in the workspace.
+// Applies the autotuned schedule of (p, m, n, form), if any, for one call and
+// restores the caller's options afterwards.
+struct TunedScope {
+  pluq_ctx* c;
+  int leaf_dim, leaf_kind, fork_depth;
+  TunedScope(pluq_ctx* ctx, int64_t m, int64_t n)
+      : c(ctx), leaf_dim(ctx->leaf_dim), leaf_kind(ctx->leaf_kind), fork_depth(ctx->fork_depth) {
+    if (c->tuning || !c->use_tuned) return;
+    for (const pluq_ctx::Tuned& t : c->tuned)
+      if (t.p == c->F.p && t.m == m && t.n == n && t.form == c->form) {
+        c->leaf_dim = t.leaf_dim;
+        c->leaf_kind = t.leaf_kind;
+        c->fork_depth = t.fork_depth;
+        break;
+      }
+  }
+  ~TunedScope() {
+    c->leaf_dim = leaf_dim;
+    c->leaf_kind = leaf_kind;
+    c->fork_depth = fork_depth;
+  }
+};
+
 int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t* r_out) {
+  TunedScope tuned(c, m, n);
   c->mmax = std::max<int64_t>(m, 1);
   c->nmax = std::max<int64_t>(n, 1);
   PLUQ_TRY(c->perm_r.ensure(sizeof(int32_t) * kMaxDepth * c->mmax));
@@ -646,6 +696,8 @@ int pluq_destroy(pluq_ctx* c) {
   c->small.release();
   c->inv_table.release();
   c->leaf.release();
+  c->tune_src.release();
+  c->tune_dst.release();
   c->tri_inv.release();
   c->batch_dev.release();
   c->batch_scratch.release();
@@ -689,32 +741,56 @@ int rank_profile_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint3
   return PLUQ_OK;
 }
 
-int echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A, int64_t lda,
-                 uint32_t* R, int64_t ldr, int64_t* rank_dev, int32_t* crp, int form, void* stream) {
-  if (!c || m < 0 || n < 0) return PLUQ_ERR_INVALID_ARG;
-  if (m > 0 && n > 0 && (!A || !R || lda < n || ldr < n)) return PLUQ_ERR_INVALID_ARG;
-  PLUQ_TRY(prepare(c, p, m, n, form, stream));
-  PLUQ_TRY(copy_to_work(c, m, n, A, lda));
+// RREF of the m x n matrix W (workspace, ld ldw, factored in place) written
+// with strides (rs, cs); rank to rank_dev, pivot columns to crp (may be NULL).
+static int echelon_core(pluq_ctx* c, int64_t m, int64_t n, uint32_t* W, int64_t ldw, uint32_t* R,
+                        int64_t rs, int64_t cs, int64_t* rank_dev, int32_t* crp) {
   int64_t r = 0;
-  uint32_t* W = c->work.as<uint32_t>();
-  const int64_t ldw = std::max<int64_t>(n, 1);
   PLUQ_TRY(factor(c, m, n, W, ldw, &r));
   PLUQ_TRY(write_outputs(c, m, n, r, nullptr, nullptr, rank_dev, nullptr, nullptr));
   if (r == 0) return PLUQ_OK;
   // X = U1^{-1} [U1 U2] in the Q frame: only U2 needs solving.
   PLUQ_TRY(trsm_left_upper(c, W, ldw, r, W + r, ldw, n - r));
-  int32_t* ints = c->tmp_i.as<int32_t>();
   PLUQ_TRY(c->tmp_i.ensure(sizeof(int32_t) * (n + r + 64)));
-  ints = c->tmp_i.as<int32_t>();
+  int32_t* ints = c->tmp_i.as<int32_t>();
   int32_t* qinv = ints;
   int32_t* crp_buf = crp ? crp : ints + n;
   const int32_t* PC = c->perm_c.as<int32_t>();
   ProfScope ps(c, PC_OTHER, 0, 8.0 * n + 4.0 * r * n, 3);
   k_invert_perm<<<(unsigned)cdiv(n, 256), 256, 0, c->stream>>>(PC, n, qinv);
   k_profile<<<1, 1024, sizeof(uint32_t) * cdiv(n, 32), c->stream>>>(PC, r, n, crp_buf);
-  k_rref_scatter<<<grid2(r, n), 256, 0, c->stream>>>(W, ldw, r, n, qinv, crp_buf, R, ldr);
+  k_rref_scatter<<<grid2(r, n), 256, 0, c->stream>>>(W, ldw, r, n, qinv, crp_buf, R, rs, cs);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
+}
+
+int echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A, int64_t lda,
+                 uint32_t* R, int64_t ldr, int64_t* rank_dev, int32_t* crp, int form, void* stream) {
+  if (!c || m < 0 || n < 0) return PLUQ_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && (!A || !R || lda < n || ldr < n)) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(prepare(c, p, m, n, form, stream));
+  PLUQ_TRY(copy_to_work(c, m, n, A, lda));
+  return echelon_core(c, m, n, c->work.as<uint32_t>(), std::max<int64_t>(n, 1), R, ldr, 1,
+                      rank_dev, crp);
+}
+
+int column_echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A,
+                        int64_t lda, uint32_t* C, int64_t ldc, int64_t* rank_dev, int32_t* rrp,
+                        int form, void* stream) {
+  if (!c || m < 0 || n < 0) return PLUQ_ERR_INVALID_ARG;
+  if (m > 0 && n > 0 && (!A || !C || lda < n || ldc < std::min(m, n))) return PLUQ_ERR_INVALID_ARG;
+  // the RREF of A^T (n x m), transposed back: E = RREF(A^T)^T, m x r
+  PLUQ_TRY(prepare(c, p, n, m, form, stream));
+  PLUQ_TRY(c->work.ensure(sizeof(uint32_t) * std::max<int64_t>(m * n, 1)));
+  uint32_t* W = c->work.as<uint32_t>();
+  const int64_t ldw = std::max<int64_t>(m, 1);
+  if (m > 0 && n > 0) {
+    ProfScope ps(c, PC_OTHER, 0, 8.0 * m * n);
+    k_transpose<<<dim3((unsigned)cdiv(n, 32), (unsigned)cdiv(m, 32)), dim3(32, 8), 0,
+                  c->stream>>>(W, ldw, A, lda, m, n);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  return echelon_core(c, n, m, W, ldw, C, 1, ldc, rank_dev, rrp);
 }
 
 int fgemm_modp(pluq_ctx* c, uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
@@ -906,6 +982,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
       if (value < 0 || value > 64) return PLUQ_ERR_INVALID_ARG;
       c->chain_rows = value;
       return PLUQ_OK;
+    case PLUQ_OPT_USE_TUNED:
+      if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;
+      c->use_tuned = value;
+      return PLUQ_OK;
     case PLUQ_OPT_FORK_DEPTH:
       if (value < 0 || value > 4) return PLUQ_ERR_INVALID_ARG;
       c->fork_depth = value;
@@ -922,6 +1002,106 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
 int pluq_set_leaf(pluq_ctx* c, int leaf_dim) {
   if (!c || leaf_dim < 0 || leaf_dim > leaf_max_dim()) return PLUQ_ERR_INVALID_ARG;
   c->leaf_dim = leaf_dim;
+  return PLUQ_OK;
+}
+
+int pluq_autotune(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A, int64_t lda,
+                  int form, void* stream, double budget_ms, int32_t* chosen, double* best_ms) {
+  if (!c || m <= 0 || n <= 0 || !A || lda < n) return PLUQ_ERR_INVALID_ARG;
+  if (m >= 0x7fffffff || n >= 0x7fffffff) return PLUQ_ERR_INVALID_ARG;
+  PLUQ_TRY(prepare(c, p, m, n, form, stream));
+  const size_t bytes = sizeof(uint32_t) * (size_t)m * n;
+  PLUQ_TRY(c->tune_src.ensure(bytes));
+  PLUQ_TRY(c->tune_dst.ensure(bytes));
+  uint32_t* src = c->tune_src.as<uint32_t>();
+  uint32_t* dst = c->tune_dst.as<uint32_t>();
+  {
+    ProfScope ps(c, PC_OTHER, 0, 8.0 * m * n);
+    k_copy_mat<<<grid2(m, n), 256, 0, c->stream>>>(src, n, A, lda, m, n);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  if (budget_ms <= 0) budget_ms = 10000.0;
+  const int save_leaf = c->leaf_dim, save_kind = c->leaf_kind, save_fork = c->fork_depth;
+  c->tuning = true;
+  // one warm run, then the best of two timed runs of a schedule (ms), or a status
+  auto trial = [&](int leaf, int kind, int fork, double* ms) -> int {
+    c->leaf_dim = leaf;
+    c->leaf_kind = kind;
+    c->fork_depth = fork;
+    double best = 1e30;
+    for (int it = 0; it < 3; ++it) {
+      PLUQ_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+      PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+      const auto t0 = std::chrono::steady_clock::now();
+      int64_t r = 0;
+      const int st = factor(c, m, n, dst, n, &r);
+      if (st != PLUQ_OK) return st;
+      const double t = std::chrono::duration<double, std::milli>(
+                           std::chrono::steady_clock::now() - t0).count();
+      if (it > 0) best = std::min(best, t);
+    }
+    *ms = best;
+    return PLUQ_OK;
+  };
+  const auto start = std::chrono::steady_clock::now();
+  auto spent = [&] {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - start)
+        .count();
+  };
+  // leaf cut-offs that differ for this shape (one at or above the larger side)
+  std::vector<int> leaves;
+  for (int l : {1024, 512, 2048}) {
+    const int64_t big = std::max(m, n);
+    bool dup = false;
+    for (int e : leaves) dup |= (e >= big && l >= big);
+    if (!dup) leaves.push_back(l);
+  }
+  int b_leaf = 1024, b_kind = 2, b_fork = 2;
+  double b_ms = 1e30;
+  int st = PLUQ_OK;
+  // stage 1: cut-off and leaf kind (the default schedule first); stage 2: fork depth
+  for (int l : leaves) {
+    for (int k : {2, 0, 1}) {
+      if (b_ms < 1e30 && spent() > budget_ms) break;
+      double ms = 0;
+      st = trial(l, k, 2, &ms);
+      if (st != PLUQ_OK) break;
+      if (ms < b_ms) {
+        b_ms = ms;
+        b_leaf = l;
+        b_kind = k;
+      }
+    }
+    if (st != PLUQ_OK) break;
+  }
+  for (int f : {0, 1, 3}) {
+    if (st != PLUQ_OK || spent() > budget_ms) break;
+    double ms = 0;
+    st = trial(b_leaf, b_kind, f, &ms);
+    if (st == PLUQ_OK && ms < b_ms) {
+      b_ms = ms;
+      b_fork = f;
+    }
+  }
+  c->tuning = false;
+  c->leaf_dim = save_leaf;
+  c->leaf_kind = save_kind;
+  c->fork_depth = save_fork;
+  if (st != PLUQ_OK) return st;
+  pluq_ctx::Tuned t{c->F.p, m, n, c->form, b_leaf, b_kind, b_fork, b_ms};
+  bool replaced = false;
+  for (pluq_ctx::Tuned& e : c->tuned)
+    if (e.p == t.p && e.m == m && e.n == n && e.form == t.form) {
+      e = t;
+      replaced = true;
+    }
+  if (!replaced) c->tuned.push_back(t);
+  if (chosen) {
+    chosen[0] = b_leaf;
+    chosen[1] = b_kind;
+    chosen[2] = b_fork;
+  }
+  if (best_ms) *best_ms = b_ms;
   return PLUQ_OK;
 }
 

@@ -224,6 +224,22 @@ def test_pluq_concurrent_branches(ctx, fork_depth, leaf, p, shape, frac):
         ctx.set_option("fork_depth", 2)
 
 
+def test_pluq_leaf_too_large_for_child_context(ctx):
+    """A block within the leaf cut-off that no leaf kernel of a child context (half
+    the SMs) can hold is split further instead of recursing on itself."""
+    m = n = 4096  # F and G are about 2000 x 2048 in contexts of half the SMs
+    g = workloads.prescribed_rank_matrix(m, n, 600, 131071, 3, device="cuda")
+    ctx.set_option("fork_depth", 2)
+    try:
+        with leaf_mode(ctx, (2048, 1)):
+            r, P, Q, LU, rrp, crp = run_pluq(ctx, g.A, 131071, "limb")
+    finally:
+        ctx.set_option("fork_depth", 2)
+    assert r == g.rank
+    check_rpm_from_pq(P, Q, r, g.rpm)
+    assert rrp.tolist() == g.rrp.tolist() and crp.tolist() == g.crp.tolist()
+
+
 @pytest.mark.parametrize("mode", [(0, (8, 8)), (0, (16, 8)), (0, (5, 13)), (0, (32, 32)),
                                   (0, (128, 64)), ((9, 0), (8, 8)), ((24, 0), (8, 8)),
                                   ((40, 0), (8, 8)), ((9, 1), (8, 8)), ((24, 1), (8, 8)),
@@ -304,6 +320,21 @@ def test_echelon_parity(ctx, p, shape, frac):
     assert crp.cpu().tolist() == g.crp.tolist()
     assert np.array_equal(R.cpu().numpy().astype(np.int64), Rref.astype(np.int64))
     check_rref(g.A, p, R.cpu().numpy(), crp.cpu().numpy())
+
+
+@pytest.mark.parametrize("p", [2, 65521, 131071, 2147483647])
+@pytest.mark.parametrize("shape,frac", [((40, 60), 0.5), ((257, 300), 0.7), ((300, 257), 1.0),
+                                        ((1, 5), 1.0), ((700, 130), 0.4)])
+def test_column_echelon_parity(ctx, p, shape, frac):
+    """Reduced column echelon form = RREF(A^T)^T; its pivot rows are the row rank profile."""
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(min(m, n) * frac), p, seed=7)
+    r, E, rrp = pq.column_echelon_modp(to_dev(g.A), p, ctx=ctx)
+    torch.cuda.synchronize()
+    rr, Rt = oracle.rref(np.ascontiguousarray(g.A.T), p)
+    assert r == rr == g.rank
+    assert rrp.cpu().tolist() == g.rrp.tolist()
+    assert np.array_equal(E.cpu().numpy().astype(np.int64), Rt.T.astype(np.int64))
 
 
 @pytest.mark.parametrize("p", [2, 131071])
@@ -523,3 +554,27 @@ def test_config_lru_16384x20480_p31(ctx, form):
     assert not np.any(LU[r:, r:])
     assert np.all(np.diag(LU[:r, :r]) != 0)
     freivalds_blocked(g.A, cfg.p, P, Q, LU, r)
+
+
+# ------------------------------------------------------------- autotuner --
+
+@pytest.mark.parametrize("p,shape,frac", [(131071, (700, 700), 0.3), (65521, (1100, 900), 1.0)])
+def test_autotune_schedule_parity(ctx, p, shape, frac):
+    """The autotuned schedule is applied to later calls of the shape and stays exact."""
+    m, n = shape
+    r = int(frac * min(m, n))
+    A = workloads.prescribed_rank_matrix(m, n, r, p, 21).A
+    Ad = to_dev(A)
+    keep = Ad.clone()
+    ch = ctx.autotune(Ad, p, form="limb", budget_ms=3000)
+    torch.cuda.synchronize()
+    assert torch.equal(Ad, keep)  # the tuner works on copies
+    assert ch["leaf_dim"] in (512, 1024, 2048)
+    assert ch["leaf_kind"] in ("barrier", "wavefront", "per-leaf")
+    assert ch["fork_depth"] in (0, 1, 2, 3) and ch["ms"] > 0
+    try:
+        assert assert_parity(ctx, A, p, "limb") == r
+        ctx.set_option("use_tuned", 0)
+        assert assert_parity(ctx, A, p, "limb") == r
+    finally:
+        ctx.set_option("use_tuned", 1)
