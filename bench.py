@@ -97,6 +97,21 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself without dist."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gfops(world: int, work_per_rank: float, ms_slowest: float) -> float:
+    """Independent replicas: the work of all ranks over the slowest rank's time."""
+    return world * work_per_rank / (ms_slowest / 1e3) / 1e9
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -225,10 +240,7 @@ def bench_batched(args, world, rank, local):
     ms_step = time_batched(plan, A, A0, args.steps, stream)
     clocks = sampler.stop()
     launches = sum(c["launches"] for c in ctx.profile_read().values())
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist, "cuda")
     # per-matrix launches on a sample of the same matrices
     sample = list(range(0, cfg.count, 32))
     A.copy_(A0)
@@ -241,7 +253,7 @@ def bench_batched(args, world, rank, local):
     F_sample = sum(field_ops(int(ms[b]), int(ns[b]), int(rs[b])) for b in sample)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(world * F / (ms_step / 1e3) / 1e9, 3), "unit": "Gfops",
+            "metric": METRIC, "value": round(whole_job_gfops(world, F, ms_step), 3), "unit": "Gfops",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -338,13 +350,11 @@ def bench_ours(args, world, rank, local):
     ms_profiled = time_steps(pq, ctx, A, A0, p, form, args.steps, stream)
     classes = ctx.profile_read()
     ctx.profile(False)
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     F = field_ops(m, n, r)
-    value = world * F / (ms / 1e3) / 1e9
+    value = whole_job_gfops(world, F, ms)
 
     # FP64-embedding form on the same input (the paper's representation)
     fp64 = None
@@ -353,7 +363,8 @@ def bench_ours(args, world, rank, local):
             A.copy_(A0)
             pq.pluq_modp(A, p, form="fp64", ctx=ctx)
         ms64 = time_steps(pq, ctx, A, A0, p, "fp64", max(1, min(args.steps, 2)), stream)
-        fp64 = {"value": round(world * F / (ms64 / 1e3) / 1e9, 3), "ms_per_step": round(ms64, 3)}
+        ms64 = max_over_ranks(ms64, dist, "cuda")
+        fp64 = {"value": round(whole_job_gfops(world, F, ms64), 3), "ms_per_step": round(ms64, 3)}
 
     # end to end through the public API: pinned host input -> device -> PLUQ ->
     # L\U, P, Q back to pinned host memory
@@ -375,10 +386,7 @@ def bench_ours(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
 
     # roofline of the dominant kernel class
     peaks = read_peaks()
@@ -427,7 +435,7 @@ def bench_ours(args, world, rank, local):
             "bitexact": exact,
             "fgemm_dtype": "f16 digits, f32 accumulate" if form != "fp64" else "f64",
             "fp64_form": fp64,
-            "e2e": {"value": round(world * F / (e2e_ms / 1e3) / 1e9, 3), "unit": "Gfops",
+            "e2e": {"value": round(whole_job_gfops(world, F, e2e_ms), 3), "unit": "Gfops",
                     "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(m * n * 4),
                     "d2h_bytes_per_step": int(m * n * 4 + 4 * (m + n))},
             "gpu_launches": int(launches),

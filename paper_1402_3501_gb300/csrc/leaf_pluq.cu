@@ -115,6 +115,8 @@ __device__ void compact_unflagged(const int32_t* flag, int count, int32_t* out, 
   __syncthreads();
 }
 
+constexpr int kLeafMaxRows = 128;  // owned rows per CTA of a barrier leaf
+
 // Words per candidate slot: the row, its live column and the Montgomery
 // inverse of its entry there, padded to 16 bytes.
 __host__ __device__ inline int leaf_slot(int n) { return (n + 2 + 3) & ~3; }
@@ -126,6 +128,8 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
                 uint32_t* __restrict__ candbuf, int* __restrict__ err) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t s_hdr[2];  // elected pivot column and Montgomery inverse
+  __shared__ int s_act[kLeafMaxRows], s_newf[kLeafMaxRows], s_nact;
+  __shared__ uint32_t s_cm[kLeafMaxRows], s_cmul[kLeafMaxRows];
   const unsigned G = gridDim.x;
   const int cta = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -218,32 +222,63 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
     __syncthreads();
     const int j0 = (int)s_hdr[0];
     const uint32_t inv_m = s_hdr[1];
-    // eliminate owned rows below the pivot row; the pivot row leaves the race
-    for (int lr = warp; lr < owned; lr += kLeafWarps) {
-      const int l = lr * (int)G + cta;
-      if (l == istar) {
-        if (lane == 0) fcol[lr] = INT_MAX;
-        continue;
+    // rows to eliminate: owned rows below the pivot row with a non-zero in its
+    // column (the others keep their first live column); the pivot row leaves
+    // the race.  Listed with their multipliers by warp 0.
+    if (warp == 0) {
+      int cnt = 0;
+      for (int b0 = 0; b0 < owned; b0 += 32) {
+        const int lr = b0 + lane;
+        bool act = false;
+        uint32_t cmul = 0, cm = 0;
+        if (lr < owned) {
+          const int l = lr * (int)G + cta;
+          if (l == istar) {
+            fcol[lr] = INT_MAX;
+          } else if (l > istar) {  // rows above are zero or pivot rows
+            const uint32_t wl = W[(size_t)lr * n + j0];
+            if (wl != 0u) {
+              act = true;
+              cmul = f_mul_mont(inv_m, wl, F);
+              cm = f_to_mont(cmul, F);
+            }
+          }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, act);
+        if (act) {
+          const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+          s_act[pos] = lr;
+          s_cm[pos] = cm;
+          s_cmul[pos] = cmul;
+          s_newf[pos] = INT_MAX;
+        }
+        cnt += __popc(mask);
       }
-      if (l < istar) continue;  // zero or pivot rows
-      uint32_t* Wl = W + (size_t)lr * n;
-      const uint32_t wl = Wl[j0];
-      if (wl == 0u) continue;  // unchanged; its first live column is not j0
-      const uint32_t cmul = f_mul_mont(inv_m, wl, F);
-      const uint32_t cm = f_to_mont(cmul, F);
+      if (lane == 0) s_nact = cnt;
+    }
+    __syncthreads();
+    // W[l, :] -= c_l piv[:], all threads over (row, column): a thread keeps
+    // the same columns for every row, its first live column per row reduced
+    // over the warp and then over the CTA
+    const int na = s_nact;
+    for (int a = 0; a < na; ++a) {
+      uint32_t* Wl = W + (size_t)s_act[a] * n;
+      const uint32_t cm = s_cm[a];
       int jl = INT_MAX;
-      for (int j = lane; j < n; j += 32) {
-        if (j == j0 || ispiv[j]) continue;
-        const uint32_t nv = f_sub(Wl[j], f_mul_mont(cm, piv[j], F), F);
-        Wl[j] = nv;
-        if (nv != 0u && jl == INT_MAX) jl = j;
+      for (int j = tid; j < n; j += kLeafThreads) {
+        if (j == j0) {
+          Wl[j] = s_cmul[a];
+        } else if (!ispiv[j]) {
+          const uint32_t nv = f_sub(Wl[j], f_mul_mont(cm, piv[j], F), F);
+          Wl[j] = nv;
+          if (nv != 0u && jl == INT_MAX) jl = j;
+        }
       }
       jl = __reduce_min_sync(0xffffffffu, jl);
-      if (lane == 0) {
-        Wl[j0] = cmul;
-        fcol[lr] = jl;
-      }
+      if (lane == 0 && jl != INT_MAX) atomicMin(&s_newf[a], jl);
     }
+    __syncthreads();
+    if (tid < na) fcol[s_act[tid]] = s_newf[tid];
     if (tid == 0) {
       prow[r] = istar;
       pcol[r] = j0;
@@ -306,6 +341,7 @@ int leaf_max_dim() { return 2048; }
 // Whether a leaf of m x n fits the shared memory of the cooperative grid.
 int leaf_fits(pluq_ctx* c, int64_t m, int64_t n) {
   if (m <= 0 || n <= 0 || m > c->leaf_dim || n > c->leaf_dim) return 0;
+  if ((m + c->sm_count - 1) / c->sm_count > kLeafMaxRows) return 0;
   return leaf_smem((int)m, (int)n, c->sm_count) <= 220 * 1024;
 }
 
@@ -323,7 +359,7 @@ int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_
     ++G;
     smem = leaf_smem(m, n, G);
   }
-  if (smem > 220 * 1024) return PLUQ_ERR_INVALID_ARG;
+  if (smem > 220 * 1024 || (m + G - 1) / G > kLeafMaxRows) return PLUQ_ERR_INVALID_ARG;
   // barrier words, election slots and two candidate-row buffers of G rows each
   if (G > kLeafMaxCtas || G > kLeafThreads) return PLUQ_ERR_INVALID_ARG;
   const size_t head = (sizeof(LeafSync) + 255) / 256 * 256;

@@ -1,0 +1,55 @@
+"""Multi-rank path of bench.py (independent replicas) on CPU with the gloo backend.
+
+Every rank factors its own matrix; the only collective is the reduction of the
+timed region to the slowest rank, and the reported value is the work of all
+ranks over that time.  Two ranks here, each with its own (deliberately unequal)
+timing; the oracle stands in for the GPU factorization so the test needs no GPU.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import oracle
+    import workloads
+    g = workloads.prescribed_rank_matrix(64, 48, 20, 65521, seed=10 + rank)
+    res = oracle.pluq(g.A, 65521)  # each rank's own replica
+    local_ms = 10.0 * (rank + 1)  # rank 1 is the slow one
+    slowest = bench.max_over_ranks(local_ms, dist, "cpu")
+    F = bench.field_ops(64, 48, res.rank)
+    out[rank] = (res.rank == g.rank and res.rpm == g.rpm, slowest,
+                 bench.whole_job_gfops(world, F, slowest))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_replicas_gloo():
+    world = 2
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    assert all(res[r][0] for r in range(world))
+    assert res[0][1] == res[1][1] == 20.0
+    F = 2 * 64 * 48 * 20 - (64 + 48) * 20 ** 2 + 2 * 20 ** 3 / 3
+    assert np.isclose(res[0][2], world * F / 0.020 / 1e9)
