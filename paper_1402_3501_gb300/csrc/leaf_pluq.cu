@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
   __shared__ int s_col[kChainBatch];
   __shared__ uint32_t s_inv[kChainBatch];
   __shared__ uint32_t s_cm[kChainBatch * 32];  // multipliers per (batch pivot, row < 32)
+  __shared__ uint32_t s_mul[kChainMaxRows], s_mulm[kChainMaxRows];  // phase-2 multipliers
   const int G = gridDim.x, cta = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int mn = min(m, n);
@@ -579,12 +580,20 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
       if (j0 == INT_MAX) continue;  // the row reduced to zero
       const uint32_t inv = f_inv(Wl[j0], F, inv_table);
       const uint32_t inv_m = f_to_mont(inv, F);
-      // publish the pivot row with its pivot-column entries zeroed
+      // publish the pivot row with its pivot-column entries zeroed; the
+      // multipliers of the own rows below it
       uint32_t* dst = pub + (size_t)np * n;
       for (int j = tid; j < n; j += kLeafThreads) {
         const uint32_t v = ispiv[j] ? 0u : Wl[j];
         U[j] = v;
         dst[j] = v;
+      }
+      const int below = own - lr - 1;
+      if (tid < below) {
+        const uint32_t wl = W[(size_t)(lr + 1 + tid) * n + j0];
+        const uint32_t cmul = ch_mulm<kIs2>(inv_m, wl, F);
+        s_mul[tid] = cmul;
+        s_mulm[tid] = f_to_mont(cmul, F);
       }
       if (tid == 0) pinfo[np] = PivInfo{r0 + lr, j0, inv_m, 0};
       __syncthreads();
@@ -593,17 +602,14 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
         __threadfence();
         chain_release(&sync->word, ((unsigned long long)cta << 32) | (unsigned)(np + 1));
       }
-      // eliminate the own rows below it
-      for (int l2 = lr + 1 + warp; l2 < own; l2 += kLeafWarps) {
-        uint32_t* W2 = W + (size_t)l2 * n;
-        const uint32_t wl = W2[j0];
-        __syncwarp();
-        if (wl == 0u) continue;
-        const uint32_t cmul = ch_mulm<kIs2>(inv_m, wl, F);
-        const uint32_t cm = f_to_mont(cmul, F);
-        for (int j = lane; j < n; j += 32) W2[j] = f_sub(W2[j], ch_mulm<kIs2>(cm, U[j], F), F);
-        __syncwarp();
-        if (lane == 0) W2[j0] = cmul;
+      // eliminate the own rows below it: all threads over (row, column), the
+      // pivot column receiving the multiplier (an L entry)
+      for (int b = 0; b < below; ++b) {
+        const uint32_t cm = s_mulm[b];
+        if (cm == 0u) continue;
+        uint32_t* W2 = W + (size_t)(lr + 1 + b) * n;
+        for (int j = tid; j < n; j += kLeafThreads)
+          W2[j] = j == j0 ? s_mul[b] : f_sub(W2[j], ch_mulm<kIs2>(cm, U[j], F), F);
       }
       __syncthreads();
       ++np;
