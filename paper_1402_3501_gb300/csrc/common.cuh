@@ -222,6 +222,12 @@ int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t co
                  const int32_t* perm);
 int permute_cols(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
                  const int32_t* perm);
+// rows of A permuted over columns [c0, c0 + n0) and [c1, c1 + n1) at once
+int permute_rows2(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t c0, int64_t n0,
+                  int64_t c1, int64_t n1, const int32_t* perm);
+// columns of A permuted over rows [r0, r0 + m0) and [r1, r1 + m1) at once
+int permute_cols2(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t r0, int64_t m0, int64_t r1,
+                  int64_t m1, int64_t cols, const int32_t* perm);
 int trsm_left_lower_unit(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r, uint32_t* B,
                          int64_t ldb, int64_t ncols);
 int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,

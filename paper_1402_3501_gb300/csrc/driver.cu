@@ -444,12 +444,12 @@ struct Recursion {
     PLUQ_TRY(launch_compose(c, pr + r1, cr + R0 + r1, m1 - r1));
     PLUQ_TRY(launch_compose(c, pc + n1, cc + C0 + n1, n2));
     PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
-    PLUQ_TRY(permute_cols(c, X(R0, C0, 0, n1), lda, r1, n2, cc + C0 + n1));       // D
-    PLUQ_TRY(permute_cols(c, X(R0, C0, m1, n1), lda, m2, n2, cc + C0 + n1));      // H
+    // D (rows 0..r1) and H (rows m1..m) by F's column permutation
+    PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
     PLUQ_TRY(launch_compose(c, pr + m1, cr + R0 + m1, m2));
     PLUQ_TRY(launch_compose(c, pc + r1, cc + C0 + r1, n1 - r1));
-    PLUQ_TRY(permute_rows(c, X(R0, C0, m1, 0), lda, m2, r1, cr + R0 + m1));   // E
-    PLUQ_TRY(permute_rows(c, X(R0, C0, m1, n1), lda, m2, n2, cr + R0 + m1));  // H
+    // E (columns 0..r1) and H (columns n1..n) by G's row permutation
+    PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
     PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
 
     // H = [H1 H2; H3 H4] at rows m1.., columns n1..
@@ -470,14 +470,12 @@ struct Recursion {
     PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4));
     PLUQ_TRY(launch_compose(c, pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3));
     PLUQ_TRY(launch_compose(c, pc + n1 + r2, cc + C0 + n1 + r2, n2 - r2));
-    PLUQ_TRY(permute_rows(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, r1 + r3,
-                          cr + R0 + m1 + r3));  // E2, M3
-    PLUQ_TRY(permute_rows(c, X(R0, C0, m1 + r3, n1), lda, m2 - r3, r2,
-                          cr + R0 + m1 + r3));  // K
-    PLUQ_TRY(permute_cols(c, X(R0, C0, 0, n1 + r2), lda, r1 + r2, n2 - r2,
-                          cc + C0 + n1 + r2));  // D2, V2
-    PLUQ_TRY(permute_cols(c, X(R0, C0, m1, n1 + r2), lda, r3, n2 - r2,
-                          cc + C0 + n1 + r2));  // O
+    // E2, M3 (columns 0..r1+r3) and K (columns n1..n1+r2) by R's row permutation
+    PLUQ_TRY(permute_rows2(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, 0, r1 + r3, n1, r2,
+                           cr + R0 + m1 + r3));
+    // D2, V2 (rows 0..r1+r2) and O (rows m1..m1+r3) by R's column permutation
+    PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1 + r2), lda, 0, r1 + r2, m1, r3, n2 - r2,
+                           cc + C0 + n1 + r2));
 
     // block-cyclic shifts
     int32_t* tmp = PR(kMaxDepth - 1) + R0;  // spare row slot (this block's range)

@@ -56,40 +56,51 @@ __global__ void k_segperm(int32_t* __restrict__ out, Segs sg, int64_t total) {
   }
 }
 
-// dst[t, :] = src[perm[t], :] (rows x cols)
-__global__ void k_gather_rows(uint32_t* __restrict__ dst, int64_t ldd,
-                              const uint32_t* __restrict__ src, int64_t lds, int64_t rows,
-                              int64_t cols, const int32_t* __restrict__ perm) {
+// Two segments of one index range: index i < len0 maps to off0 + i, index
+// i >= len0 to off1 + (i - len0).  A permutation applied to two disjoint
+// column (or row) ranges of the same rows (columns) takes one pass.
+struct Seg2 {
+  int64_t len0, off0, off1;
+  __device__ __forceinline__ int64_t at(int64_t i) const {
+    return i < len0 ? off0 + i : off1 + (i - len0);
+  }
+};
+
+// S[t, u] = A[perm[t], cs.at(u)]: rows permuted, over two column segments
+__global__ void k_gather_rows(uint32_t* __restrict__ S, const uint32_t* __restrict__ A, int64_t lda,
+                              int64_t rows, int64_t cols, Seg2 cs,
+                              const int32_t* __restrict__ perm) {
   for (int64_t t = blockIdx.y; t < rows; t += gridDim.y) {
-    const uint32_t* s = src + (int64_t)perm[t] * lds;
-    uint32_t* d = dst + t * ldd;
+    const uint32_t* s = A + (int64_t)perm[t] * lda;
+    uint32_t* d = S + t * cols;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
          u += (int64_t)gridDim.x * blockDim.x)
-      d[u] = s[u];
+      d[u] = s[cs.at(u)];
   }
 }
 
-// dst[t, u] = src[t, perm[u]]
-__global__ void k_gather_cols(uint32_t* __restrict__ dst, int64_t ldd,
-                              const uint32_t* __restrict__ src, int64_t lds, int64_t rows,
-                              int64_t cols, const int32_t* __restrict__ perm) {
+// S[t, u] = A[rs.at(t), perm[u]]: columns permuted, over two row segments
+__global__ void k_gather_cols(uint32_t* __restrict__ S, const uint32_t* __restrict__ A, int64_t lda,
+                              int64_t rows, int64_t cols, Seg2 rs,
+                              const int32_t* __restrict__ perm) {
   for (int64_t t = blockIdx.y; t < rows; t += gridDim.y) {
-    const uint32_t* s = src + t * lds;
-    uint32_t* d = dst + t * ldd;
+    const uint32_t* s = A + rs.at(t) * lda;
+    uint32_t* d = S + t * cols;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
          u += (int64_t)gridDim.x * blockDim.x)
       d[u] = s[perm[u]];
   }
 }
 
-__global__ void k_copy2d(uint32_t* __restrict__ dst, int64_t ldd, const uint32_t* __restrict__ src,
-                         int64_t lds, int64_t rows, int64_t cols) {
+// A[rs.at(t), cs.at(u)] = S[t, u]
+__global__ void k_scatter_back(uint32_t* __restrict__ A, int64_t lda, const uint32_t* __restrict__ S,
+                               int64_t rows, int64_t cols, Seg2 rs, Seg2 cs) {
   for (int64_t t = blockIdx.y; t < rows; t += gridDim.y) {
-    const uint32_t* s = src + t * lds;
-    uint32_t* d = dst + t * ldd;
+    const uint32_t* s = S + t * cols;
+    uint32_t* d = A + rs.at(t) * lda;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
          u += (int64_t)gridDim.x * blockDim.x)
-      d[u] = s[u];
+      d[cs.at(u)] = s[u];
   }
 }
 
@@ -143,28 +154,42 @@ int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const in
   return PLUQ_OK;
 }
 
-int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
-                 const int32_t* perm) {
+int permute_rows2(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t c0, int64_t n0,
+                  int64_t c1, int64_t n1, const int32_t* perm) {
+  const int64_t cols = n0 + n1;
   if (rows <= 1 || cols <= 0) return PLUQ_OK;
   PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
   uint32_t* S = c->scratch.as<uint32_t>();
+  const Seg2 cs{n0, c0, c1}, rs{rows, 0, 0};
   const dim3 g = grid2d(rows, cols, 256);
   ProfScope ps(c, PC_PERM, 0, 8.0 * rows * cols, 2);
-  k_gather_rows<<<g, 256, 0, c->stream>>>(S, cols, A, lda, rows, cols, perm);
-  k_copy2d<<<g, 256, 0, c->stream>>>(A, lda, S, cols, rows, cols);
+  k_gather_rows<<<g, 256, 0, c->stream>>>(S, A, lda, rows, cols, cs, perm);
+  k_scatter_back<<<g, 256, 0, c->stream>>>(A, lda, S, rows, cols, rs, cs);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
 
-int permute_cols(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
-                 const int32_t* perm) {
+int permute_cols2(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t r0, int64_t m0, int64_t r1,
+                  int64_t m1, int64_t cols, const int32_t* perm) {
+  const int64_t rows = m0 + m1;
   if (rows <= 0 || cols <= 1) return PLUQ_OK;
   PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
   uint32_t* S = c->scratch.as<uint32_t>();
+  const Seg2 rs{m0, r0, r1}, cs{cols, 0, 0};
   const dim3 g = grid2d(rows, cols, 256);
   ProfScope ps(c, PC_PERM, 0, 8.0 * rows * cols, 2);
-  k_gather_cols<<<g, 256, 0, c->stream>>>(S, cols, A, lda, rows, cols, perm);
-  k_copy2d<<<g, 256, 0, c->stream>>>(A, lda, S, cols, rows, cols);
+  k_gather_cols<<<g, 256, 0, c->stream>>>(S, A, lda, rows, cols, rs, perm);
+  k_scatter_back<<<g, 256, 0, c->stream>>>(A, lda, S, rows, cols, rs, cs);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
+}
+
+int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
+                 const int32_t* perm) {
+  return permute_rows2(c, A, lda, rows, 0, cols, 0, 0, perm);
+}
+
+int permute_cols(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,
+                 const int32_t* perm) {
+  return permute_cols2(c, A, lda, 0, rows, 0, 0, cols, perm);
 }

@@ -30,61 +30,72 @@ template <bool kUpper, bool kUnit>
 __global__ void __launch_bounds__(kInvThreads)
     k_tri_inv(const uint32_t* __restrict__ T, int64_t ldt, int r, int tb,
               uint32_t* __restrict__ out, FieldP F, const uint32_t* __restrict__ inv_table) {
+  // M and Y hold Montgomery forms (x R mod p): a sum of h <= 32 products of
+  // two such forms, reduced once by REDC, is the Montgomery form of the sum of
+  // the plain products (exact while the sum stays below p R: p < 2^26), else
+  // one REDC per product.  p = 2: plain bits, the parity of the sum.
   __shared__ uint32_t M[kTB][kTB + 1];
   __shared__ uint32_t Y[kTB][kTB + 1];
   const int b = blockIdx.x, tid = threadIdx.x;
   const int o = b * tb;
   const int s = min(tb, r - o);
-  const bool big = F.p >= (1u << 26);  // 32 products of residues overflow 64 bits
+  const bool big = F.p >= (1u << 26);
+  const uint32_t one_m = f_to_mont(1u, F);
   // M = lower form of the block (T, or T^T for an upper block), identity padded
-  for (int idx = tid; idx < kTB * kTB; idx += kInvThreads) {
-    const int i = idx / kTB, k = idx % kTB;
-    uint32_t v = 0;
-    if (i < s && k < s && k <= i) v = kUpper ? T[(int64_t)(o + k) * ldt + o + i] : T[(int64_t)(o + i) * ldt + o + k];
-    if (i == k) v = (i >= s || kUnit) ? 1u : f_inv(v, F, inv_table);
-    M[i][k] = v;
+  for (int idx0 = tid; idx0 < kTB * kTB; idx0 += 4 * kInvThreads) {
+    uint32_t v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = idx0 + q * kInvThreads, i = idx / kTB, k = idx % kTB;
+      v[q] = 0;
+      if (idx < kTB * kTB && i < s && k < s && k <= i)
+        v[q] = kUpper ? T[(int64_t)(o + k) * ldt + o + i] : T[(int64_t)(o + i) * ldt + o + k];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = idx0 + q * kInvThreads, i = idx / kTB, k = idx % kTB;
+      if (idx >= kTB * kTB) continue;
+      uint32_t w;
+      if (i == k)
+        w = (i >= s || kUnit) ? one_m : f_to_mont(f_inv(v[q], F, inv_table), F);
+      else
+        w = f_to_mont(v[q], F);
+      M[i][k] = w;
+    }
   }
   __syncthreads();
+  auto dot = [&](const uint32_t* a, int sa, const uint32_t* x, int sx, int len) -> uint32_t {
+    if (!big) {
+      uint64_t acc = 0;
+      for (int k = 0; k < len; ++k) acc += (uint64_t)a[k * sa] * x[k * sx];
+      return F.is2 ? (uint32_t)(acc & 1u) : f_redc(acc, F);
+    }
+    uint32_t acc = 0;
+    for (int k = 0; k < len; ++k) acc = f_add(acc, f_redc((uint64_t)a[k * sa] * x[k * sx], F), F);
+    return acc;
+  };
   for (int h = 1; h < kTB; h <<= 1) {
     // Y = C A^{-1} for every pair; C = M[B rows, A cols] (original entries)
     const int npairs = kTB / (2 * h), outs = npairs * h * h;
     for (int idx = tid; idx < outs; idx += kInvThreads) {
       const int q = idx / (h * h), rem = idx % (h * h), i = rem / h, j = rem % h;
       const int a0 = 2 * q * h, b0 = a0 + h;
-      uint32_t v;
-      if (!big) {
-        uint64_t acc = 0;
-        for (int k = j; k < h; ++k) acc += (uint64_t)M[b0 + i][a0 + k] * M[a0 + k][a0 + j];
-        v = f_reduce64(acc, F);
-      } else {
-        v = 0;
-        for (int k = j; k < h; ++k) v = f_add(v, f_mul(M[b0 + i][a0 + k], M[a0 + k][a0 + j], F), F);
-      }
-      Y[b0 + i][a0 + j] = v;
+      // A^{-1} is lower: only k >= j contribute
+      Y[b0 + i][a0 + j] = dot(&M[b0 + i][a0 + j], 1, &M[a0 + j][a0 + j], kTB + 1, h - j);
     }
     __syncthreads();
-    // X = -B^{-1} Y into C's place
+    // X = -B^{-1} Y into C's place (B^{-1} lower: k <= i)
     for (int idx = tid; idx < outs; idx += kInvThreads) {
       const int q = idx / (h * h), rem = idx % (h * h), i = rem / h, j = rem % h;
       const int a0 = 2 * q * h, b0 = a0 + h;
-      uint32_t v;
-      if (!big) {
-        uint64_t acc = 0;
-        for (int k = 0; k <= i; ++k) acc += (uint64_t)M[b0 + i][b0 + k] * Y[b0 + k][a0 + j];
-        v = f_reduce64(acc, F);
-      } else {
-        v = 0;
-        for (int k = 0; k <= i; ++k) v = f_add(v, f_mul(M[b0 + i][b0 + k], Y[b0 + k][a0 + j], F), F);
-      }
-      M[b0 + i][a0 + j] = f_sub(0u, v, F);
+      M[b0 + i][a0 + j] = f_sub(0u, dot(&M[b0 + i][b0], 1, &Y[b0][a0 + j], kTB + 1, i + 1), F);
     }
     __syncthreads();
   }
   uint32_t* dst = out + (size_t)b * kTB * kTB;
   for (int idx = tid; idx < kTB * kTB; idx += kInvThreads) {
     const int i = idx / kTB, k = idx % kTB;
-    const uint32_t v = kUpper ? M[k][i] : M[i][k];
-    dst[idx] = f_to_mont(v, F);
+    dst[idx] = kUpper ? M[k][i] : M[i][k];
   }
 }
 
