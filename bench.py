@@ -316,7 +316,14 @@ def bench_ours(args, world, rank, local):
     # schedule chosen by the library's autotuner on this matrix (untimed), then
     # warm-up (not timed) and bit-exact validation against the construction
     schedule = None
-    if not args.no_autotune:
+    if args.schedule:
+        leaf, kind, fork = (int(x) for x in args.schedule.split(","))
+        ctx.set_option("leaf_dim", leaf)
+        ctx.set_option("leaf_kind", kind)
+        ctx.set_option("fork_depth", fork)
+        schedule = {"leaf_dim": leaf, "leaf_kind": ctx.LEAF_KINDS[kind], "fork_depth": fork,
+                    "set": "by --schedule"}
+    elif not args.no_autotune:
         schedule = ctx.autotune(A0, p, form=form, budget_ms=args.tune_budget_ms)
     for _ in range(args.warmup):
         A.copy_(A0)
@@ -464,6 +471,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default schedule instead of the autotuned one")
     ap.add_argument("--tune-budget-ms", type=float, default=15000.0)
+    ap.add_argument("--schedule", default="",
+                    help="leaf_dim,leaf_kind,fork_depth to time instead of autotuning "
+                         "(leaf kind 0 barrier, 1 wavefront, 2 per leaf)")
     ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS),
                     help="matrix to factor (the default is the measured workload; the "
                          "others serve as small profiling cases)")

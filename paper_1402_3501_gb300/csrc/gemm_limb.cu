@@ -42,6 +42,7 @@ namespace {
 constexpr int kTM = 128, kTN = 128, kTK = 64;  // CTA tile, K block (one 128B swizzle row)
 constexpr int kLimbBits = 8;
 constexpr int kGemmThreads = 320;               // 10 warps
+constexpr int kBandTiles = 8;                    // tile rows per rasterization band
 constexpr int kTileBytes = kTM * kTK * 2;        // 16 KiB per digit plane tile
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -198,7 +199,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * TN;
+  // grouped rasterization: consecutive CTAs walk down a band of kBandTiles
+  // tile rows before moving right, so the CTAs resident at once share a few A
+  // and B panels in L2 instead of streaming all of B once per tile row
+  const int tiles_n = gridDim.x, tiles_m = gridDim.y;
+  const int lin = blockIdx.y * tiles_n + blockIdx.x;
+  const int band = lin / (kBandTiles * tiles_n);
+  const int first_m = band * kBandTiles;
+  const int band_h = min(tiles_m - first_m, kBandTiles);
+  const int in_band = lin - band * kBandTiles * tiles_n;
+  const int m0 = (first_m + in_band % band_h) * kTM, n0 = (in_band / band_h) * TN;
   const int num_groups = (num_kb + group_kb - 1) / group_kb;
 
   if (threadIdx.x == 0) {
