@@ -37,10 +37,8 @@ constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s
 // the barrier of step s + 1 and so finished reading step s's slots.
 constexpr int kLeafMaxCtas = 256;
 struct LeafSync {
-  unsigned count;
-  unsigned gen;
-  int abort;
-  int pad[29];
+  unsigned count;  // grid-barrier arrivals; bit 31: abort
+  int pad[31];
   int cand[2][kLeafMaxCtas];
 };
 
@@ -55,30 +53,37 @@ __device__ __forceinline__ int ld_volatile_i(const int* p) {
 }
 
 // Grid-wide barrier for a cooperative launch; false once any CTA aborted.
-__device__ bool grid_barrier(LeafSync* s, unsigned G, unsigned& gen, int* err) {
+// Grid-wide barrier: one monotonic arrival counter.  Each CTA adds 1 with a
+// release atomic (publishing the CTA's writes, ordered before it by the block
+// barrier) and polls with acquire loads until the counter reaches G times the
+// number of barriers passed; no reset, no generation word, no separate fence.
+// Bit 31 of the counter is the abort flag (a timed-out CTA sets it), seen by
+// the same polls.  false once any CTA aborted.
+constexpr unsigned kAbortBit = 0x80000000u;
+
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ bool grid_barrier(LeafSync* s, unsigned G, unsigned& target, int* err) {
   __shared__ int aborted;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned arrived = atomicAdd(&s->count, 1u);
-    if (arrived == G - 1) {
-      s->count = 0;
-      __threadfence();
-      atomicAdd(&s->gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (ld_acquire(&s->gen) == gen) {
-        if (ld_volatile_i(&s->abort)) break;
-        if (clock64() - t0 > kBarrierCycles) {
-          atomicExch(err, PLUQ_ERR_TIMEOUT);
-          atomicExch(&s->abort, 1);
-          break;
-        }
+    target += G;
+    unsigned v = atom_add_release(&s->count, 1u) + 1u;
+    const long long t0 = clock64();
+    while ((v & ~kAbortBit) < target && !(v & kAbortBit)) {
+      if (clock64() - t0 > kBarrierCycles) {
+        atomicExch(err, PLUQ_ERR_TIMEOUT);
+        atomicOr(&s->count, kAbortBit);
+        v = kAbortBit;
+        break;
       }
+      v = ld_acquire(&s->count);
     }
-    ++gen;
-    __threadfence();
-    aborted = ld_volatile_i(&s->abort);
+    aborted = (v & kAbortBit) != 0;
   }
   __syncthreads();
   return aborted == 0;
@@ -206,9 +211,9 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
     return best;
   };
 
-  unsigned gen = 0;
+  unsigned target = 0;  // grid-barrier arrivals expected so far
   publish(0);
-  bool ok = grid_barrier(sync, G, gen, err);
+  bool ok = grid_barrier(sync, G, target, err);
 
   int r = 0;
   for (int k = 0; ok; ++k) {
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
     __syncthreads();
     publish((k + 1) & 1);
     ++r;
-    ok = grid_barrier(sync, G, gen, err);
+    ok = grid_barrier(sync, G, target, err);
   }
   if (!ok || ld_volatile_i(err) != 0) return;
 
@@ -319,11 +324,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
 }
 
 __global__ void k_leaf_init(LeafSync* s) {
-  if (threadIdx.x == 0) {
-    s->count = 0u;
-    s->gen = 0u;
-    s->abort = 0;
-  }
+  if (threadIdx.x == 0) s->count = 0u;
   for (int i = threadIdx.x; i < kLeafMaxCtas; i += blockDim.x) s->cand[0][i] = s->cand[1][i] = INT_MAX;
 }
 
