@@ -477,8 +477,11 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
       unsigned long long w = chain_acquire(&sync->word);
       const long long t0 = clock64();
       bool ok = true;
-      while ((int)(w >> 32) < need_done && (int)(w & 0xffffffffu) < need_piv) {
-        if (ld_volatile_i(&sync->abort) || clock64() - t0 > kBarrierCycles) {
+      // the abort flag is an error path: checked every 32nd poll only, so a
+      // poll is one L2 round trip
+      for (unsigned it = 1; (int)(w >> 32) < need_done && (int)(w & 0xffffffffu) < need_piv;
+           ++it) {
+        if ((it & 31u) == 0 && (ld_volatile_i(&sync->abort) || clock64() - t0 > kBarrierCycles)) {
           if (!ld_volatile_i(&sync->abort)) atomicExch(err, PLUQ_ERR_TIMEOUT);
           atomicExch(&sync->abort, 1);
           ok = false;
@@ -600,7 +603,8 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
       __syncthreads();
       if (tid == 0) {
         ispiv[j0] = 1;
-        __threadfence();
+        // the release store publishes the row written by the whole CTA
+        // (ordered before it by the block barrier)
         chain_release(&sync->word, ((unsigned long long)cta << 32) | (unsigned)(np + 1));
       }
       // eliminate the own rows below it: all threads over (row, column), the
@@ -615,10 +619,8 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
       __syncthreads();
       ++np;
     }
-    if (tid == 0) {
-      __threadfence();
+    if (tid == 0)
       chain_release(&sync->word, ((unsigned long long)(cta + 1) << 32) | (unsigned)np);
-    }
   }
 
   // phase 3: once every CTA is done, write the own rows in the (P, Q) frame
