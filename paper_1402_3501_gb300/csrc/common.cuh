@@ -216,6 +216,11 @@ size_t batched_desc_size();
 void batched_fill_desc(void* out, int i, uint32_t* A, int32_t* P, int32_t* Q, int64_t lda, int m,
                        int n);
 int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t count);
+// (base_r, perm_r) and (base_c, perm_c) composed in one launch when both fit
+int launch_compose_pair(pluq_ctx* c, int32_t* base_r, const int32_t* perm_r, int64_t count_r,
+                        int32_t* base_c, const int32_t* perm_c, int64_t count_c);
+int launch_iota_pair(pluq_ctx* c, int32_t* dst_r, int64_t count_r, int32_t* dst_c,
+                     int64_t count_c);
 int launch_segperm(pluq_ctx* c, int32_t* out, const int64_t* seg_start, const int64_t* seg_len,
                    int nseg);
 int permute_rows(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t cols,

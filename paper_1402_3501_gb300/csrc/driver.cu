@@ -366,8 +366,7 @@ struct Recursion {
     int32_t* pc = PC(d) + C0;
     *r_out = 0;
     if (m == 0 || n == 0) {
-      PLUQ_TRY(launch_iota(c, pr, m));
-      PLUQ_TRY(launch_iota(c, pc, n));
+      PLUQ_TRY(launch_iota_pair(c, pr, m, pc, n));
       return PLUQ_OK;
     }
     // wavefront leaves win on dense blocks, barrier leaves on rank-deficient
@@ -408,14 +407,12 @@ struct Recursion {
     const int64_t m2 = m - m1, n2 = n - n1;
     int32_t* cr = PR(d + 1);
     int32_t* cc = PC(d + 1);
-    PLUQ_TRY(launch_iota(c, pr, m));
-    PLUQ_TRY(launch_iota(c, pc, n));
+    PLUQ_TRY(launch_iota_pair(c, pr, m, pc, n));
 
     // A1
     int64_t r1 = 0;
     PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1));
-    PLUQ_TRY(launch_compose(c, pr, cr + R0, m1));
-    PLUQ_TRY(launch_compose(c, pc, cc + C0, n1));
+    PLUQ_TRY(launch_compose_pair(c, pr, cr + R0, m1, pc, cc + C0, n1));
     PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
     PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
     if (r1 > 0) {
@@ -441,13 +438,11 @@ struct Recursion {
       PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2));
       PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3));
     }
-    PLUQ_TRY(launch_compose(c, pr + r1, cr + R0 + r1, m1 - r1));
-    PLUQ_TRY(launch_compose(c, pc + n1, cc + C0 + n1, n2));
+    PLUQ_TRY(launch_compose_pair(c, pr + r1, cr + R0 + r1, m1 - r1, pc + n1, cc + C0 + n1, n2));
     PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
     // D (rows 0..r1) and H (rows m1..m) by F's column permutation
     PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
-    PLUQ_TRY(launch_compose(c, pr + m1, cr + R0 + m1, m2));
-    PLUQ_TRY(launch_compose(c, pc + r1, cc + C0 + r1, n1 - r1));
+    PLUQ_TRY(launch_compose_pair(c, pr + m1, cr + R0 + m1, m2, pc + r1, cc + C0 + r1, n1 - r1));
     // E (columns 0..r1) and H (columns n1..n) by G's row permutation
     PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
     PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
@@ -468,8 +463,8 @@ struct Recursion {
     // R
     int64_t r4 = 0;
     PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4));
-    PLUQ_TRY(launch_compose(c, pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3));
-    PLUQ_TRY(launch_compose(c, pc + n1 + r2, cc + C0 + n1 + r2, n2 - r2));
+    PLUQ_TRY(launch_compose_pair(c, pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3, pc + n1 + r2,
+                                 cc + C0 + n1 + r2, n2 - r2));
     // E2, M3 (columns 0..r1+r3) and K (columns n1..n1+r2) by R's row permutation
     PLUQ_TRY(permute_rows2(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, 0, r1 + r3, n1, r2,
                            cr + R0 + m1 + r3));

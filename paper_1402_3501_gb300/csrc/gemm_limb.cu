@@ -24,9 +24,9 @@
 //              and of B^T into a shared-memory ring (6, 3, 3 or 2 stages for L = 1..4);
 //   warp 1     TMEM allocation and the single MMA-issuing thread;
 //   warps 2-9  epilogue: two warps per TMEM lane quadrant, 64 columns each.
-// The digit planes are written by a packing pass into workspace.  Every
-// mbarrier wait is bounded; on expiry the kernel records PLUQ_ERR_TIMEOUT in
-// the error word, drains, frees TMEM and returns.
+// The digit planes of both operands are written by one packing launch into
+// workspace.  Every mbarrier wait is bounded; on expiry the kernel records
+// PLUQ_ERR_TIMEOUT in the error word, drains, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -406,12 +406,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // Digit planes of A (M x K) in K-major layout: out[l][i][k], rows padded to
 // Mp and columns to Kp with zeros.
 template <int L>
-__global__ void k_pack_rows(const uint32_t* __restrict__ A, int64_t lda, int64_t M, int64_t K,
-                            int64_t Mp, int64_t Kp, uint32_t p, __half* __restrict__ out) {
+__device__ __forceinline__ void pack_rows(const uint32_t* __restrict__ A, int64_t lda, int64_t M,
+                                          int64_t K, int64_t Mp, int64_t Kp, uint32_t p,
+                                          __half* __restrict__ out, int bx, int by, int gx,
+                                          int gy, int tid, int nthreads) {
   const int64_t half_p = (p - 1) / 2;
-  for (int64_t i = blockIdx.y; i < Mp; i += gridDim.y)
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Kp;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = by; i < Mp; i += gy)
+  for (int64_t k = (int64_t)bx * nthreads + tid; k < Kp; k += (int64_t)gx * nthreads) {
     int32_t x = 0;
     if (i < M && k < K) {
       const int64_t a = A[i * lda + k];
@@ -434,11 +435,12 @@ __global__ void k_pack_rows(const uint32_t* __restrict__ A, int64_t lda, int64_t
 // Digit planes of B^T: B is K x N row-major; out[l][j][k] (K-major rows of
 // B^T), padded to Np x Kp.  32 x 32 tiles transposed through shared memory.
 template <int L>
-__global__ void k_pack_cols(const uint32_t* __restrict__ B, int64_t ldb, int64_t K, int64_t N,
-                            int64_t Np, int64_t Kp, uint32_t p, __half* __restrict__ out) {
+__device__ __forceinline__ void pack_cols(const uint32_t* __restrict__ B, int64_t ldb, int64_t K,
+                                          int64_t N, int64_t Np, int64_t Kp, uint32_t p,
+                                          __half* __restrict__ out, int bx, int by, int tx,
+                                          int ty) {
   __shared__ int32_t tile[32][33];
-  const int64_t k0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t k0 = (int64_t)bx * 32, j0 = (int64_t)by * 32;  // 32 x 8 threads
   const int64_t half_p = (p - 1) / 2;
   for (int yy = ty; yy < 32; yy += 8) {
     const int64_t k = k0 + yy, j = j0 + tx;
@@ -466,6 +468,42 @@ __global__ void k_pack_cols(const uint32_t* __restrict__ B, int64_t ldb, int64_t
       out[(int64_t)l * Np * Kp + j * Kp + k] = __int2half_rn(d);
     }
   }
+}
+
+// Both operands' digit planes in one launch: z = 0 packs A (grid ga), z = 1
+// packs B^T (grid gb, 32 x 8 threads as 256); blocks outside a part's grid
+// return at once.
+struct PackGrid {
+  int x, y;
+};
+
+template <int L>
+__global__ void __launch_bounds__(256)
+    k_pack_both(const uint32_t* __restrict__ A, int64_t lda, int64_t M, int64_t Mp,
+                const uint32_t* __restrict__ B, int64_t ldb, int64_t N, int64_t Np, int64_t K,
+                int64_t Kp, uint32_t p, __half* __restrict__ outA, __half* __restrict__ outB,
+                PackGrid ga, PackGrid gb) {
+  if (blockIdx.z == 0) {
+    if ((int)blockIdx.x >= ga.x || (int)blockIdx.y >= ga.y) return;
+    pack_rows<L>(A, lda, M, K, Mp, Kp, p, outA, blockIdx.x, blockIdx.y, ga.x, ga.y, threadIdx.x,
+                 256);
+  } else {
+    if ((int)blockIdx.x >= gb.x || (int)blockIdx.y >= gb.y) return;
+    pack_cols<L>(B, ldb, K, N, Np, Kp, p, outB, blockIdx.x, blockIdx.y, threadIdx.x & 31,
+                 threadIdx.x >> 5);
+  }
+}
+
+template <int L>
+int launch_pack(cudaStream_t s, const uint32_t* A, int64_t lda, int64_t M, int64_t Mp,
+                const uint32_t* B, int64_t ldb, int64_t N, int64_t Np, int64_t K, int64_t Kp,
+                uint32_t p, __half* Ap, __half* Bp) {
+  const PackGrid ga{(int)std::min<int64_t>(cdiv(Kp, 256), 64), (int)std::min<int64_t>(Mp, 65535)};
+  const PackGrid gb{(int)cdiv(Kp, 32), (int)cdiv(Np, 32)};
+  const dim3 g((unsigned)std::max(ga.x, gb.x), (unsigned)std::max(ga.y, gb.y), 2);
+  k_pack_both<L><<<g, 256, 0, s>>>(A, lda, M, Mp, B, ldb, N, Np, K, Kp, p, Ap, Bp, ga, gb);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
 }
 
 // ------------------------------------------------------------ host side --
@@ -597,12 +635,9 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   __half* Ap = c->pack.as<__half>();
   __half* Bp = reinterpret_cast<__half*>(reinterpret_cast<char*>(Ap) + ((abytes + 1023) / 1024) * 1024);
   {
-    ProfScope ps(c, PC_PACK, 0, 4.0 * (M * K + K * N) + (double)abytes + (double)bbytes, 2);
-    dim3 g((unsigned)std::min<int64_t>(cdiv(Kp, 256), 64), (unsigned)std::min<int64_t>(Mp, 65535));
-    k_pack_rows<L><<<g, 256, 0, c->stream>>>(A, lda, M, K, Mp, Kp, c->F.p, Ap);
-    dim3 g2((unsigned)cdiv(Kp, 32), (unsigned)cdiv(Np, 32));
-    k_pack_cols<L><<<g2, dim3(32, 8), 0, c->stream>>>(B, ldb, K, N, Np, Kp, c->F.p, Bp);
-    PLUQ_CUDA(cudaGetLastError());
+    ProfScope ps(c, PC_PACK, 0, 4.0 * (M * K + K * N) + (double)abytes + (double)bbytes, 1);
+    if (cdiv(Np, 32) > 65535) return PLUQ_ERR_INVALID_ARG;
+    PLUQ_TRY(launch_pack<L>(c->stream, A, lda, M, Mp, B, ldb, N, Np, K, Kp, c->F.p, Ap, Bp));
   }
   CUtensorMap ma, mb;
   PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp, kTM));
@@ -723,11 +758,7 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
   __half* Ap = reinterpret_cast<__half*>(d.scratch);
   __half* Bp = reinterpret_cast<__half*>(d.scratch + aoff);
   PLUQ_CUDA(cudaMemsetAsync(d.err, 0, sizeof(int), s));
-  dim3 g((unsigned)std::min<int64_t>(cdiv(Kp, 256), 64), (unsigned)std::min<int64_t>(Mp, 65535));
-  k_pack_rows<L><<<g, 256, 0, s>>>(A, lda, M, K, Mp, Kp, F.p, Ap);
-  dim3 g2((unsigned)cdiv(Kp, 32), (unsigned)cdiv(Np, 32));
-  k_pack_cols<L><<<g2, dim3(32, 8), 0, s>>>(B, ldb, K, N, Np, Kp, F.p, Bp);
-  PLUQ_CUDA(cudaGetLastError());
+  PLUQ_TRY(launch_pack<L>(s, A, lda, M, Mp, B, ldb, N, Np, K, Kp, F.p, Ap, Bp));
   CUtensorMap ma, mb;
   PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp, kTM));
   PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp, TN));

@@ -7,6 +7,8 @@
 // coalesced read and write per element) and copied back, because the
 // permutations of the recursion are arbitrary (pivots interleaved with the
 // rest) and in-place cycle following does not vectorise.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -23,6 +25,28 @@ __global__ void k_compose_smem(int32_t* __restrict__ base, const int32_t* __rest
   for (int t = threadIdx.x; t < count; t += blockDim.x) s[t] = base[perm[t]];
   __syncthreads();
   for (int t = threadIdx.x; t < count; t += blockDim.x) base[t] = s[t];
+}
+
+// The row and the column index vectors of a node in one launch: block 0
+// composes (base_r, perm_r), block 1 (base_c, perm_c); each <= 12288 entries.
+__global__ void k_compose_pair(int32_t* __restrict__ base_r, const int32_t* __restrict__ perm_r,
+                               int count_r, int32_t* __restrict__ base_c,
+                               const int32_t* __restrict__ perm_c, int count_c) {
+  extern __shared__ int32_t s[];
+  int32_t* base = blockIdx.x == 0 ? base_r : base_c;
+  const int32_t* perm = blockIdx.x == 0 ? perm_r : perm_c;
+  const int count = blockIdx.x == 0 ? count_r : count_c;
+  for (int t = threadIdx.x; t < count; t += blockDim.x) s[t] = base[perm[t]];
+  __syncthreads();
+  for (int t = threadIdx.x; t < count; t += blockDim.x) base[t] = s[t];
+}
+
+// dst_r[i] = i (i < count_r) and dst_c[j] = j (j < count_c) in one launch
+__global__ void k_iota_pair(int32_t* __restrict__ dst_r, int64_t count_r,
+                            int32_t* __restrict__ dst_c, int64_t count_c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count_r) dst_r[i] = (int32_t)i;
+  if (i < count_c) dst_c[i] = (int32_t)i;
 }
 
 __global__ void k_compose_gather(int32_t* __restrict__ out, const int32_t* __restrict__ base,
@@ -133,6 +157,30 @@ int launch_compose(pluq_ctx* c, int32_t* base, const int32_t* perm, int64_t coun
     k_compose_gather<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(tmp, base, perm, count);
     k_copy_i32<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(base, tmp, count);
   }
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int launch_compose_pair(pluq_ctx* c, int32_t* base_r, const int32_t* perm_r, int64_t count_r,
+                        int32_t* base_c, const int32_t* perm_c, int64_t count_c) {
+  if (count_r > 12288 || count_c > 12288 || count_r <= 1 || count_c <= 1) {
+    PLUQ_TRY(launch_compose(c, base_r, perm_r, count_r));
+    return launch_compose(c, base_c, perm_c, count_c);
+  }
+  ProfScope ps(c, PC_INDEX, 0, 12.0 * (count_r + count_c));
+  const size_t smem = sizeof(int32_t) * (size_t)std::max(count_r, count_c);
+  k_compose_pair<<<2, 1024, smem, c->stream>>>(base_r, perm_r, (int)count_r, base_c, perm_c,
+                                               (int)count_c);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+int launch_iota_pair(pluq_ctx* c, int32_t* dst_r, int64_t count_r, int32_t* dst_c,
+                     int64_t count_c) {
+  const int64_t count = std::max(count_r, count_c);
+  if (count <= 0) return PLUQ_OK;
+  ProfScope ps(c, PC_INDEX, 0, 4.0 * (count_r + count_c));
+  k_iota_pair<<<(unsigned)cdiv(count, 256), 256, 0, c->stream>>>(dst_r, count_r, dst_c, count_c);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
