@@ -129,6 +129,7 @@ struct pluq_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;  // a child context's stream
   cudaEvent_t fork_ev = nullptr;      // recorded before F and G start
+  cudaEvent_t side_ev[2] = {nullptr, nullptr};  // E ready, G updated (two-stream update)
   FieldP F{};
   int form = PLUQ_FORM_FP64;
   int bm = 128, bn = 128;  // base-case tile

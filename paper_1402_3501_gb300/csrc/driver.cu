@@ -203,6 +203,10 @@ __global__ void k_transpose(uint32_t* __restrict__ dst, int64_t ldd,
 
 __global__ void k_store_rank(int64_t* dst, int64_t r) { *dst = r; }
 
+__global__ void k_merge_err(int* dst, const int* src) {
+  if (*src != 0 && *dst == 0) *dst = *src;
+}
+
 dim3 grid2(int64_t rows, int64_t cols) {
   int64_t gx = cdiv(cols, 256);
   if (gx > 32) gx = 32;
@@ -237,6 +241,8 @@ void destroy_lane(pluq_ctx* l) {
   l->work.release();
   for (cudaEvent_t e : l->prof.pool) cudaEventDestroy(e);
   if (l->fork_ev) cudaEventDestroy(l->fork_ev);
+  for (cudaEvent_t e : l->side_ev)
+    if (e) cudaEventDestroy(e);
   if (l->host_small) cudaFreeHost(l->host_small);
   if (l->own_stream) cudaStreamDestroy(l->own_stream);
   delete l;
@@ -289,7 +295,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   PLUQ_TRY(l->tmp_i.ensure(sizeof(int32_t) * std::max(c->mmax, c->nmax)));
   PLUQ_TRY(l->tri_inv.ensure(sizeof(uint32_t) * cdiv(mn, std::max(1, c->trsm_block)) * 64 * 64));
   if (c->form == PLUQ_FORM_LIMB_F16) {
-    const int64_t kp = cdiv(mn / 2 + 64, 64) * 64;
+    const int64_t kp = cdiv(mn + 64, 64) * 64;
     const int64_t rows = cdiv(m, 128) * 128 + cdiv(n, 128) * 128;
     PLUQ_TRY(l->pack.ensure(sizeof(uint16_t) * 4 * rows * kp + 4096));
   }
@@ -361,6 +367,38 @@ struct Recursion {
     return st_f != PLUQ_OK ? st_f : st_g;
   }
 
+  // The updates after A1 on two streams (see node); returns once this
+  // context's stream waits for the other's work (no host synchronisation).
+  int side_stream_update(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2,
+                         int64_t r1) {
+    const int64_t m = m1 + m2;
+    pluq_ctx* lg = nullptr;
+    PLUQ_TRY(get_lane(c, 1, m2, n1, &lg));
+    for (cudaEvent_t* e : {&c->fork_ev, &c->side_ev[0], &c->side_ev[1]})
+      if (!*e) PLUQ_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    PLUQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+    PLUQ_CUDA(cudaStreamWaitEvent(lg->stream, c->fork_ev, 0));
+    // G's stream: E, then G -= E V1
+    PLUQ_TRY(trsm_right_upper(lg, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2));
+    PLUQ_CUDA(cudaEventRecord(c->side_ev[0], lg->stream));
+    PLUQ_TRY(fgemm_sub(lg, m2, n1 - r1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, r1), lda,
+                       X(R0, C0, m1, r1), lda));
+    PLUQ_CUDA(cudaEventRecord(c->side_ev[1], lg->stream));
+    // this stream: D, then [F; H] -= [M1; E] D once E is ready
+    PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2));
+    PLUQ_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[0], 0));
+    PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
+                       X(R0, C0, r1, n1), lda));
+    PLUQ_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[1], 0));
+    // the other stream's device error word joins this context's
+    k_merge_err<<<1, 1, 0, c->stream>>>(c->small.as<int>() + 16, lg->small.as<int>() + 16);
+    PLUQ_CUDA(cudaGetLastError());
+    merge_lane_stats(c, lg);
+    for (int k = 0; k < PC_COUNT; ++k) lg->launches[k] = 0;
+    lg->n_base = lg->n_nodes = lg->n_gemm = 0;
+    return PLUQ_OK;
+  }
+
   int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out) {
     int32_t* pr = PR(d) + R0;
     int32_t* pc = PC(d) + C0;
@@ -416,12 +454,21 @@ struct Recursion {
     PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
     PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
     if (r1 > 0) {
-      PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2));
-      PLUQ_TRY(trsm_right_upper(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2));
-      PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
-                         X(R0, C0, r1, n1), lda));
-      PLUQ_TRY(fgemm_sub(c, m2, n1 - r1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, r1), lda,
-                         X(R0, C0, m1, r1), lda));
+      // D = L1^{-1} B1 and E = C1 U1^{-1} are independent, and so is G's
+      // update (it needs E only): E and G -= E V1 go to the G child context's
+      // stream while this one solves D, then [F; H] -= [M1; E] D waits for E
+      const bool side = c->lane_depth < c->fork_depth && !c->prof.on && m2 > 0 &&
+                        (int64_t)r1 * (m2 + n2) >= kForkMinElems * 64;
+      if (side) {
+        PLUQ_TRY(side_stream_update(R0, C0, m1, n1, m2, n2, r1));
+      } else {
+        PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2));
+        PLUQ_TRY(trsm_right_upper(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2));
+        PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
+                           X(R0, C0, r1, n1), lda));
+        PLUQ_TRY(fgemm_sub(c, m2, n1 - r1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, r1), lda,
+                           X(R0, C0, m1, r1), lda));
+      }
     }
 
     // F (rows r1..m1 of the top half, right columns) and G (bottom rows,
@@ -680,6 +727,8 @@ int pluq_destroy(pluq_ctx* c) {
   destroy_lane(c->lane[0]);
   destroy_lane(c->lane[1]);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  for (cudaEvent_t e : c->side_ev)
+    if (e) cudaEventDestroy(e);
   c->scratch.release();
   c->pack.release();
   c->perm_r.release();
