@@ -211,6 +211,11 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        on its own stream, host thread and workspace with
  *                        half the SMs for its leaves; 0 runs them in turn.
  *                        Profiling (pluq_profile_enable) runs them in turn.
+ *   PLUQ_OPT_THIN_GEMM   1 (default): in the limb form, Schur updates with an
+ *                        inner dimension K <= 128 (and K p < 2^31) run on the
+ *                        CUDA cores (exact 64-bit sums, one reduction per
+ *                        entry) instead of packing digits for the tensor
+ *                        cores; 0: every update on the tensor cores.
  *   PLUQ_OPT_USE_TUNED   1 (default): factorizations whose (p, m, n, form)
  *                        was autotuned use the tuned schedule in place of
  *                        LEAF_DIM, LEAF_KIND and FORK_DEPTH; 0: ignore it.
@@ -223,6 +228,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_CHAIN_ROWS 6
 #define PLUQ_OPT_FORK_DEPTH 7
 #define PLUQ_OPT_USE_TUNED 8
+#define PLUQ_OPT_THIN_GEMM 9
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

@@ -141,7 +141,7 @@ class Context:
             pass
 
     OPTIONS = {"leaf_dim": 1, "leaf_kind": 2, "tile_m": 3, "tile_n": 4, "trsm_block": 5,
-               "chain_rows": 6, "fork_depth": 7, "use_tuned": 8}
+               "chain_rows": 6, "fork_depth": 7, "use_tuned": 8, "thin_gemm": 9}
 
     def set_option(self, name: str, value: int):
         """Set a recursion option (see PLUQ_OPT_* in include/pluqmodp.h)."""

@@ -168,6 +168,7 @@ struct pluq_ctx {
   // the parent's index-vector slots and inverse table (disjoint ranges /
   // read-only) and cooperative leaves in a child use at most its sm_count
   int fork_depth = 2;             // levels of the recursion that run F and G concurrently
+  int thin_gemm = 1;              // limb form: CUDA-core fgemm for K <= kThinMaxK
   int lane_depth = 0;             // 0 for the user's context
   pluq_ctx* parent = nullptr;
   pluq_ctx* lane[2] = {nullptr, nullptr};
@@ -243,6 +244,11 @@ int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint
 // C <- C - A B (mod p); A M x K, B K x N, C M x N, all row-major uint32.
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
+// the same on the CUDA cores for a thin inner dimension (K <= kThinMaxK, K p < 2^31)
+constexpr int64_t kThinMaxK = 128;
+int thin_fgemm_ok(const pluq_ctx* c, int64_t K);
+int fgemm_sub_thin(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
+                   const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
 int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,
                    int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
 int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,

@@ -276,6 +276,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->leaf_density = c->leaf_density;
   l->chain_rows = c->chain_rows;
   l->fork_depth = c->fork_depth;
+  l->thin_gemm = c->thin_gemm;
   l->mmax = c->mmax;
   l->nmax = c->nmax;
   l->limb_plan_p = c->limb_plan_p;
@@ -694,7 +695,11 @@ int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, i
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
   c->n_gemm++;
-  if (c->form == PLUQ_FORM_LIMB_F16) return fgemm_sub_limb(c, M, N, K, A, lda, B, ldb, C, ldc);
+  if (c->form == PLUQ_FORM_LIMB_F16) {
+    // a thin inner dimension does not pay for packing and a tensor pipeline
+    if (c->thin_gemm && thin_fgemm_ok(c, K)) return fgemm_sub_thin(c, M, N, K, A, lda, B, ldb, C, ldc);
+    return fgemm_sub_limb(c, M, N, K, A, lda, B, ldb, C, ldc);
+  }
   return fgemm_sub_fp64(c, M, N, K, A, lda, B, ldb, C, ldc);
 }
 
@@ -1023,6 +1028,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_CHAIN_ROWS:
       if (value < 0 || value > 64) return PLUQ_ERR_INVALID_ARG;
       c->chain_rows = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_THIN_GEMM:
+      if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;
+      c->thin_gemm = value;
       return PLUQ_OK;
     case PLUQ_OPT_USE_TUNED:
       if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;

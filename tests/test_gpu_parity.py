@@ -76,6 +76,30 @@ def assert_parity(ctx, A, p, form="auto", expect=None):
 
 # ---------------------------------------------------------------- fgemm ----
 
+@pytest.mark.parametrize("thin", [1, 0])
+def test_fgemm_thin_and_tensor_paths(ctx, thin):
+    """Inner dimensions around the CUDA-core / tensor-core switch (K = 128), both
+    paths forced in turn, ragged tiles, extreme residues."""
+    ctx.set_option("thin_gemm", thin)
+    try:
+        for p in (2, 65521, 131071, 16777213):
+            for (M, N, K) in [(1, 1, 1), (65, 63, 31), (200, 130, 127), (129, 257, 128),
+                              (70, 300, 129)]:
+                rng = np.random.default_rng(M + 3 * N + 7 * K + p % 89)
+                A = rng.integers(0, p, (M, K), dtype=np.int64)
+                B = rng.integers(0, p, (K, N), dtype=np.int64)
+                C = rng.integers(0, p, (M, N), dtype=np.int64)
+                A[0, :] = p - 1
+                B[:, 0] = p - 1
+                expect = (C - matmul_mod(A, B, p)) % p
+                Cd = to_dev(C)
+                pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form="limb", ctx=ctx)
+                torch.cuda.synchronize()
+                assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), (p, M, N, K)
+    finally:
+        ctx.set_option("thin_gemm", 1)
+
+
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("p", [2, 3, 251, 65521, 131071])
 @pytest.mark.parametrize("mnk", [(1, 1, 1), (70, 33, 17), (129, 257, 100), (300, 200, 700),
@@ -205,6 +229,18 @@ def test_pluq_large_primes(ctx, form, p, shape, frac):
         else:
             A = workloads.prescribed_rank_matrix(m, n, r, p, 5).A
             assert assert_parity(ctx, A, p, form) == r
+
+
+@pytest.mark.parametrize("thin", [0, 1])
+def test_pluq_thin_gemm_switch(ctx, thin):
+    """The factorization is the same whether thin Schur updates use the CUDA cores."""
+    g = workloads.prescribed_rank_matrix(700, 650, 300, 131071, 12)
+    ctx.set_option("thin_gemm", thin)
+    try:
+        with leaf_mode(ctx, 96, tiles=(64, 64)):
+            assert assert_parity(ctx, g.A, 131071, "limb") == 300
+    finally:
+        ctx.set_option("thin_gemm", 1)
 
 
 @pytest.mark.parametrize("fork_depth", [0, 1, 4])
