@@ -212,10 +212,11 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        half the SMs for its leaves; 0 runs them in turn.
  *                        Profiling (pluq_profile_enable) runs them in turn.
  *   PLUQ_OPT_THIN_GEMM   1 (default): in the limb form, Schur updates with an
- *                        inner dimension K <= 128 (and K p < 2^31) run on the
- *                        CUDA cores (exact 64-bit sums, one reduction per
- *                        entry) instead of packing digits for the tensor
- *                        cores; 0: every update on the tensor cores.
+ *                        inner dimension K <= 128 (and K p < 2^31) and at most
+ *                        2^27 multiply-adds run on the CUDA cores (exact
+ *                        64-bit sums, one reduction per entry) instead of
+ *                        packing digits for the tensor cores; 0: every update
+ *                        on the tensor cores.
  *   PLUQ_OPT_USE_TUNED   1 (default): factorizations whose (p, m, n, form)
  *                        was autotuned use the tuned schedule in place of
  *                        LEAF_DIM, LEAF_KIND and FORK_DEPTH; 0: ignore it.

@@ -244,9 +244,10 @@ int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint
 // C <- C - A B (mod p); A M x K, B K x N, C M x N, all row-major uint32.
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
-// the same on the CUDA cores for a thin inner dimension (K <= kThinMaxK, K p < 2^31)
+// the same on the CUDA cores for a thin inner dimension (K <= kThinMaxK,
+// K p < 2^31) and small total work
 constexpr int64_t kThinMaxK = 128;
-int thin_fgemm_ok(const pluq_ctx* c, int64_t K);
+int thin_fgemm_ok(const pluq_ctx* c, int64_t M, int64_t N, int64_t K);
 int fgemm_sub_thin(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
                    const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
 int fgemm_sub_fp64(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,

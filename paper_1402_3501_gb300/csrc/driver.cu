@@ -697,7 +697,8 @@ int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, i
   c->n_gemm++;
   if (c->form == PLUQ_FORM_LIMB_F16) {
     // a thin inner dimension does not pay for packing and a tensor pipeline
-    if (c->thin_gemm && thin_fgemm_ok(c, K)) return fgemm_sub_thin(c, M, N, K, A, lda, B, ldb, C, ldc);
+    if (c->thin_gemm && thin_fgemm_ok(c, M, N, K))
+      return fgemm_sub_thin(c, M, N, K, A, lda, B, ldb, C, ldc);
     return fgemm_sub_limb(c, M, N, K, A, lda, B, ldb, C, ldc);
   }
   return fgemm_sub_fp64(c, M, N, K, A, lda, B, ldb, C, ldc);

@@ -80,8 +80,11 @@ __global__ void __launch_bounds__(kThinThreads)
 
 }  // namespace
 
-int thin_fgemm_ok(const pluq_ctx* c, int64_t K) {
-  return K > 0 && K <= kThinMaxK && (uint64_t)K * c->F.p < (1ull << 31);
+// Worth it while the CUDA-core work stays below the tensor path's fixed cost
+// (a packing pass and a pipeline fill, about 20 us): about 2^27 multiply-adds.
+int thin_fgemm_ok(const pluq_ctx* c, int64_t M, int64_t N, int64_t K) {
+  return K > 0 && K <= kThinMaxK && (uint64_t)K * c->F.p < (1ull << 31) &&
+         (double)M * N * K <= 134217728.0;
 }
 
 int fgemm_sub_thin(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
