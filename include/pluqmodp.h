@@ -181,6 +181,22 @@ int pluq_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const int64_t* m
                       int32_t* const* P, int32_t* const* Q, int64_t* ranks, int32_t* status,
                       int form, void* stream);
 
+/* Rank and both rank profiles of every matrix of a batch (the batched form of
+ * rank_profile_modp, Sec. 4.1): pluq_modp_batched on the matrices, then one
+ * launch sorting each matrix's pivot rows and columns.  A[b] is overwritten
+ * with its compressed L\U, as in pluq_modp_batched; the permutations go to a
+ * workspace of the context.
+ *   rrp, crp host arrays of batch device pointers (either array may be NULL;
+ *            an entry may be NULL): int32, length >= min(m[b], n[b]); receive
+ *            the sorted row and column rank profiles.
+ *   ranks    host, batch entries; -1 for a matrix that failed.
+ *   status   host, batch entries (may be NULL).
+ * Other arguments and errors as pluq_modp_batched.  Synchronises the stream. */
+int rank_profile_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const int64_t* m,
+                              const int64_t* n, uint32_t* const* A, const int64_t* lda,
+                              int32_t* const* rrp, int32_t* const* crp, int64_t* ranks,
+                              int32_t* status, int form, void* stream);
+
 /* Host copy of the rank found by the last factorization on this context. */
 int pluq_last_rank(pluq_ctx* ctx, int64_t* rank);
 

@@ -8,11 +8,12 @@ binding (binding.py).
 """
 from .binding import (BatchPlan, FORM_AUTO, FORM_FP64, FORM_LIMB_F16, Context, PluqError, PLUQResult,
                       column_echelon_modp, default_context, echelon_modp, fgemm_modp,
-                      fgemm_modp_noalloc, load, pluq_modp, pluq_modp_batched, rank_profile_modp)
+                      fgemm_modp_noalloc, load, pluq_modp, pluq_modp_batched, rank_profile_modp,
+                      rank_profile_modp_batched)
 
 __all__ = [
     "BatchPlan",
     "FORM_AUTO", "FORM_FP64", "FORM_LIMB_F16", "Context", "PluqError", "PLUQResult",
     "column_echelon_modp", "default_context", "echelon_modp", "fgemm_modp", "fgemm_modp_noalloc",
-    "load", "pluq_modp", "pluq_modp_batched", "rank_profile_modp",
+    "load", "pluq_modp", "pluq_modp_batched", "rank_profile_modp", "rank_profile_modp_batched",
 ]

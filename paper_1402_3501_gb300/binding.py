@@ -36,6 +36,7 @@ SYMBOLS = [
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
     "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
     "fgemm_modp_noalloc", "pluq_set_option", "pluq_autotune", "column_echelon_modp",
+    "rank_profile_modp_batched",
 ]
 
 
@@ -64,6 +65,8 @@ def load():
         "rank_profile_modp": [vp, u32, i64, i64, vp, i64, vp, vp, vp, vp, i32, vp],
         "fgemm_modp": [vp, u32, i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp],
         "pluq_modp_batched": [vp, u32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp],
+        "rank_profile_modp_batched": [vp, u32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32,
+                                      vp],
         "pluq_last_rank": [vp, vp],
         "pluq_set_tuning": [vp, i32, i32, i32],
         "pluq_last_stats": [vp, vp, vp, vp],
@@ -395,6 +398,43 @@ def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None,
     if return_status:
         return outs + (list(status),)
     _check(st, "pluq_modp_batched")
+    return outs
+
+
+def rank_profile_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None,
+                              stream=None, return_status: bool = False):
+    """Ranks and sorted row / column rank profiles of a list of CUDA int32 matrices
+    (factored in place): (ranks, rrps, crps[, status])."""
+    if not As:
+        return ([], [], [], []) if return_status else ([], [], [])
+    ctx = ctx or default_context(As[0].device.index)
+    b = len(As)
+    ms = (ctypes.c_int64 * b)()
+    ns = (ctypes.c_int64 * b)()
+    lds = (ctypes.c_int64 * b)()
+    aptr = (ctypes.c_void_p * b)()
+    rptr = (ctypes.c_void_p * b)()
+    cptr = (ctypes.c_void_p * b)()
+    ranks = (ctypes.c_int64 * b)()
+    status = (ctypes.c_int32 * b)()
+    R, Cc = [], []
+    for i, A in enumerate(As):
+        m, n, ld = _matrix_args(A)
+        ms[i], ns[i], lds[i] = m, n, ld
+        aptr[i] = A.data_ptr() if A.numel() else None
+        rr = torch.empty(max(min(m, n), 1), dtype=torch.int32, device=A.device)
+        cc = torch.empty(max(min(m, n), 1), dtype=torch.int32, device=A.device)
+        R.append(rr)
+        Cc.append(cc)
+        rptr[i] = rr.data_ptr()
+        cptr[i] = cc.data_ptr()
+    st = load().rank_profile_modp_batched(ctx.handle, p, b, ms, ns, aptr, lds, rptr, cptr, ranks,
+                                          status, _form(form), _stream_handle(stream))
+    rk = list(ranks)
+    outs = (rk, [R[i][:max(rk[i], 0)] for i in range(b)], [Cc[i][:max(rk[i], 0)] for i in range(b)])
+    if return_status:
+        return outs + (list(status),)
+    _check(st, "rank_profile_modp_batched")
     return outs
 
 

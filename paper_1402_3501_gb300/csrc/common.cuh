@@ -159,6 +159,7 @@ struct pluq_ctx {
   uint32_t batch_graph_p = 0;        // field and inverse table baked into the graph
   const void* batch_graph_tab = nullptr;
   DevBuf batch_scratch;    // per-CTA gather scratch of the batched kernel
+  DevBuf batch_pq;         // pivot vectors and profile descriptors of a batched rank profile
   const void* batch_graph_key = nullptr;
   int32_t* host_small = nullptr;  // pinned host scalars
   uint32_t limb_plan_p = 0;       // p of the cached limb fgemm plan

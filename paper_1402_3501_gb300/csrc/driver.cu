@@ -104,9 +104,10 @@ __global__ void k_copy_mat(uint32_t* __restrict__ dst, int64_t ldd, const uint32
 
 // Sorted set of the first r entries of a permutation of [0, cnt): a bitmap in
 // shared memory, then an ordered compaction (one CTA).
-__global__ void k_profile(const int32_t* __restrict__ perm, int64_t r, int64_t cnt,
-                          int32_t* __restrict__ out) {
-  extern __shared__ uint32_t bits[];
+// out[0..r) = the first r entries of perm (distinct, < cnt) in increasing
+// order, by a bitmap in shared memory and a block prefix count.
+__device__ void sorted_profile(const int32_t* __restrict__ perm, int64_t r, int64_t cnt,
+                               int32_t* __restrict__ out, uint32_t* bits) {
   __shared__ int32_t warp_tot[32];
   const int64_t words = (cnt + 31) / 32;
   for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
@@ -148,6 +149,33 @@ __global__ void k_profile(const int32_t* __restrict__ perm, int64_t r, int64_t c
       out[pos++] = (int32_t)(w * 32 + bit);
       b &= b - 1;
     }
+  }
+}
+
+__global__ void k_profile(const int32_t* __restrict__ perm, int64_t r, int64_t cnt,
+                          int32_t* __restrict__ out) {
+  extern __shared__ uint32_t bits[];
+  sorted_profile(perm, r, cnt, out, bits);
+}
+
+// Row and column rank profiles of a batch: block (b, 0) sorts matrix b's
+// pivot rows, block (b, 1) its pivot columns.
+struct ProfileDesc {
+  const int32_t* P;
+  const int32_t* Q;
+  int32_t* rrp;
+  int32_t* crp;
+  int64_t m, n, r;
+};
+
+__global__ void k_profiles_batched(const ProfileDesc* __restrict__ d) {
+  extern __shared__ uint32_t bits[];
+  const ProfileDesc e = d[blockIdx.x];
+  if (e.r <= 0) return;
+  if (blockIdx.y == 0) {
+    if (e.rrp) sorted_profile(e.P, e.r, e.m, e.rrp, bits);
+  } else {
+    if (e.crp) sorted_profile(e.Q, e.r, e.n, e.crp, bits);
   }
 }
 
@@ -749,6 +777,7 @@ int pluq_destroy(pluq_ctx* c) {
   c->tri_inv.release();
   c->batch_dev.release();
   c->batch_scratch.release();
+  c->batch_pq.release();
   if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
   if (c->batch_host) cudaFreeHost(c->batch_host);
   c->work.release();
@@ -989,6 +1018,57 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
     if (st != PLUQ_OK && first_bad == PLUQ_OK) first_bad = st;
   }
   return first_bad;
+}
+
+int rank_profile_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m,
+                              const int64_t* n, uint32_t* const* A, const int64_t* lda,
+                              int32_t* const* rrp, int32_t* const* crp, int64_t* ranks,
+                              int32_t* status, int form, void* stream) {
+  if (!c || batch < 0 || (batch > 0 && (!m || !n || !A || !lda || !ranks)))
+    return PLUQ_ERR_INVALID_ARG;
+  if (batch == 0) return PLUQ_OK;
+  // pivot index vectors of every matrix in one workspace
+  std::vector<int64_t> offp(batch), offq(batch);
+  int64_t total = 0, maxdim = 1;
+  for (int32_t b = 0; b < batch; ++b) {
+    const int64_t mb = std::max<int64_t>(m[b], 0), nb = std::max<int64_t>(n[b], 0);
+    offp[b] = total;
+    total += mb;
+    offq[b] = total;
+    total += nb;
+    maxdim = std::max(maxdim, std::max(mb, nb));
+  }
+  PLUQ_TRY(c->batch_pq.ensure(sizeof(int32_t) * std::max<int64_t>(total, 1) +
+                              sizeof(ProfileDesc) * batch + 256));
+  int32_t* base = c->batch_pq.as<int32_t>();
+  std::vector<int32_t*> Pp(batch), Qp(batch);
+  for (int32_t b = 0; b < batch; ++b) {
+    Pp[b] = base + offp[b];
+    Qp[b] = base + offq[b];
+  }
+  const int st = pluq_modp_batched(c, p, batch, m, n, A, lda, Pp.data(), Qp.data(), ranks, status,
+                                   form, stream);
+  if (st != PLUQ_OK && st != PLUQ_ERR_INVALID_ARG && st != PLUQ_ERR_ENTRY_OUT_OF_RANGE) return st;
+  // profiles of the matrices that factored (ranks < 0 mark the others)
+  std::vector<ProfileDesc> d(batch);
+  for (int32_t b = 0; b < batch; ++b)
+    d[b] = ProfileDesc{Pp[b], Qp[b], rrp ? rrp[b] : nullptr, crp ? crp[b] : nullptr,
+                       std::max<int64_t>(m[b], 0), std::max<int64_t>(n[b], 0),
+                       ranks[b] > 0 ? ranks[b] : 0};
+  ProfileDesc* dd = reinterpret_cast<ProfileDesc*>(
+      reinterpret_cast<char*>(base) + ((sizeof(int32_t) * std::max<int64_t>(total, 1) + 255) / 256) * 256);
+  PLUQ_CUDA(cudaMemcpyAsync(dd, d.data(), sizeof(ProfileDesc) * batch, cudaMemcpyHostToDevice,
+                            c->stream));
+  const size_t smem = sizeof(uint32_t) * cdiv(maxdim, 32);
+  if (smem > 48 * 1024) return PLUQ_ERR_INVALID_ARG;
+  {
+    ProfScope ps(c, PC_OTHER, 0, 8.0 * total);
+    k_profiles_batched<<<dim3((unsigned)batch, 2), 256, smem, c->stream>>>(dd);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  // the descriptors are host vectors: wait for the copy before they go away
+  PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+  return st;
 }
 
 int pluq_last_rank(pluq_ctx* c, int64_t* rank) {

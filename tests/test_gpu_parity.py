@@ -482,6 +482,23 @@ def test_batched_parity(ctx, p):
             check_pluq(A, p, P, Q, Ad.cpu().numpy().astype(np.int64), r)
 
 
+@pytest.mark.parametrize("p", [2, 65521])
+def test_rank_profile_batched(ctx, p):
+    """Batched ranks and sorted profiles equal the construction's, matrix by matrix,
+    including matrices past the persistent kernel's size (factored one by one)."""
+    shapes = [(40, 60, 20), (512, 300, 250), (33, 33, 33), (1, 7, 1), (600, 700, 100),
+              (128, 96, 0)]
+    gens = [workloads.prescribed_rank_matrix(m, n, r, p, 30 + i) for i, (m, n, r) in
+            enumerate(shapes)]
+    As = [to_dev(g.A) for g in gens]
+    ranks, rrps, crps = pq.rank_profile_modp_batched(As, p, ctx=ctx)
+    torch.cuda.synchronize()
+    for g, r, rr, cc in zip(gens, ranks, rrps, crps):
+        assert r == g.rank
+        assert rr.cpu().tolist() == g.rrp.tolist()
+        assert cc.cpu().tolist() == g.crp.tolist()
+
+
 def test_batched_bad_entry_status(ctx):
     p = 65521
     good = workloads.prescribed_rank_matrix(50, 60, 20, p, seed=1).A
