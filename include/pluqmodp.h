@@ -210,7 +210,8 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        (default 1024); 0 sends the recursion down to
  *                        one-CTA tiles
  *   PLUQ_OPT_LEAF_KIND   leaf kernel [0, 2]: 0 one grid barrier per pivot
- *                        (rows dealt cyclically over the CTAs), 1 block-row
+ *                        (rows dealt cyclically over the CTAs; rows that
+ *                        reduce to zero cost nothing more), 1 block-row
  *                        wavefront (each CTA applies the earlier CTAs'
  *                        pivot rows as they are published, then factors its
  *                        own rows; one hand-off per CTA; faster on dense
@@ -249,9 +250,8 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a
- * cooperative grid over all SMs (pivot search and elimination with one grid
- * barrier per pivot); 0 disables leaves so the recursion descends to
- * one-CTA base-case tiles.  Default 2048. */
+ * cooperative grid (the same as PLUQ_OPT_LEAF_DIM); 0 disables leaves so the
+ * recursion descends to one-CTA base-case tiles.  Default 1024. */
 int pluq_set_leaf(pluq_ctx* ctx, int leaf_dim);
 
 /* Counters of the last call: base-case launches, internal recursion nodes,
