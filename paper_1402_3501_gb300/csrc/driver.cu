@@ -361,7 +361,8 @@ struct Recursion {
               int d, int64_t* r2, int64_t* r3) {
     pluq_ctx* lf = nullptr;
     pluq_ctx* lg = nullptr;
-    PLUQ_TRY(get_lane(c, 0, m1 - r1, n2, &lf));
+    // F's lane also runs f_post: D and H (r1 + m2 rows) by F's columns
+    PLUQ_TRY(get_lane(c, 0, std::max(m1 - r1, m2 + r1), n2, &lf));
     PLUQ_TRY(get_lane(c, 1, m2, n1 - r1, &lg));
     if (!c->fork_ev) PLUQ_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
     PLUQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
@@ -385,7 +386,9 @@ struct Recursion {
         return;
       }
       Recursion rf{lf, A, lda, lf->small.as<int32_t>() + 8};
-      st_f = finish(lf, rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2));
+      int st = rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2);
+      if (st == PLUQ_OK) st = rf.f_post(R0, C0, m1, n1, m2, n2, r1, *r2, d);
+      st_f = finish(lf, st);
     });
     Recursion rg{lg, A, lda, lg->small.as<int32_t>() + 8};
     st_g = finish(lg, rg.node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, r3));
@@ -394,6 +397,29 @@ struct Recursion {
     merge_lane_stats(c, lg);
     c->leaf_density = lg->leaf_density;
     return st_f != PLUQ_OK ? st_f : st_g;
+  }
+
+  // What follows F and needs nothing of G: F's permutations of the blocks
+  // beside it (M1; D and H by its columns) and the first H steps,
+  // [I; K] = H[:, :r2] U2^{-1} and H[:, r2:] -= [I; K] V2.  Both act on H
+  // row by row, so they commute with G's later row permutation of H and run
+  // in F's branch while G is still being factored.
+  int f_post(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2, int64_t r1,
+             int64_t r2, int d) {
+    int32_t* pr = PR(d) + R0;
+    int32_t* pc = PC(d) + C0;
+    int32_t* cr = PR(d + 1);
+    int32_t* cc = PC(d + 1);
+    PLUQ_TRY(launch_compose_pair(c, pr + r1, cr + R0 + r1, m1 - r1, pc + n1, cc + C0 + n1, n2));
+    PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
+    // D (rows 0..r1) and H (rows m1..m) by F's column permutation
+    PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
+    if (r2 > 0) {
+      PLUQ_TRY(trsm_right_upper(c, X(R0, C0, r1, n1), lda, r2, X(R0, C0, m1, n1), lda, m2));
+      PLUQ_TRY(fgemm_sub(c, m2, n2 - r2, r2, X(R0, C0, m1, n1), lda, X(R0, C0, r1, n1 + r2), lda,
+                         X(R0, C0, m1, n1 + r2), lda));
+    }
+    return PLUQ_OK;
   }
 
   // The updates after A1 on two streams (see node); returns once this
@@ -509,26 +535,20 @@ struct Recursion {
     const bool fork = c->lane_depth < c->fork_depth && !c->prof.on &&
                       (m1 - r1) * n2 >= fork_min && m2 * (n1 - r1) >= fork_min;
     if (fork) {
+      // F's branch also runs f_post (see there)
       PLUQ_TRY(fork_fg(R0, C0, m1, n1, m2, n2, r1, d, &r2, &r3));
     } else {
       PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2));
+      PLUQ_TRY(f_post(R0, C0, m1, n1, m2, n2, r1, r2, d));
       PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3));
     }
-    PLUQ_TRY(launch_compose_pair(c, pr + r1, cr + R0 + r1, m1 - r1, pc + n1, cc + C0 + n1, n2));
-    PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
-    // D (rows 0..r1) and H (rows m1..m) by F's column permutation
-    PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
     PLUQ_TRY(launch_compose_pair(c, pr + m1, cr + R0 + m1, m2, pc + r1, cc + C0 + r1, n1 - r1));
     // E (columns 0..r1) and H (columns n1..n) by G's row permutation
     PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
     PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
 
-    // H = [H1 H2; H3 H4] at rows m1.., columns n1..
-    if (r2 > 0) {
-      PLUQ_TRY(trsm_right_upper(c, X(R0, C0, r1, n1), lda, r2, X(R0, C0, m1, n1), lda, m2));
-      PLUQ_TRY(fgemm_sub(c, m2, n2 - r2, r2, X(R0, C0, m1, n1), lda, X(R0, C0, r1, n1 + r2), lda,
-                         X(R0, C0, m1, n1 + r2), lda));
-    }
+    // H = [H1 H2; H3 H4] at rows m1.., columns n1.. ([I; K] and H2 are done
+    // in f_post): O = L3^{-1} H[:r3, r2:], R -= M3 O
     if (r3 > 0) {
       PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, m1, r1), lda, r3, X(R0, C0, m1, n1 + r2), lda,
                                     n2 - r2));
