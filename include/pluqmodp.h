@@ -209,7 +209,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *   PLUQ_OPT_LEAF_DIM    largest leaf block, rows and columns [0, 2048]
  *                        (default 1024); 0 sends the recursion down to
  *                        one-CTA tiles
- *   PLUQ_OPT_LEAF_KIND   leaf kernel [0, 2]: 0 one grid barrier per pivot
+ *   PLUQ_OPT_LEAF_KIND   leaf kernel [0, 3]: 0 one grid barrier per pivot
  *                        (rows dealt cyclically over the CTAs; rows that
  *                        reduce to zero cost nothing more), 1 block-row
  *                        wavefront (each CTA applies the earlier CTAs'
@@ -217,7 +217,13 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        own rows; one hand-off per CTA; faster on dense
  *                        blocks), 2 (default) wavefront while the previous
  *                        leaf of the call had rank density above 1/2, else
- *                        barrier
+ *                        kind 3 where the block fits it, else barrier; 3 one
+ *                        cluster barrier per pivot (the
+ *                        block in the shared memory of one thread-block
+ *                        cluster of up to 16 CTAs, candidates and the
+ *                        elected row read from the other CTAs' shared
+ *                        memory; blocks up to 1024 x 1024 for p < 2^24,
+ *                        smaller ones above; larger blocks take kind 0)
  *   PLUQ_OPT_TILE_M/N    one-CTA base-case tile [1, 128]
  *   PLUQ_OPT_TRSM_BLOCK  diagonal block of the triangular solves [1, 64]
  *                        (each block is inverted, then applied as a product)
@@ -261,8 +267,8 @@ int pluq_last_stats(pluq_ctx* ctx, int64_t* n_base, int64_t* n_nodes, int64_t* n
 /* Autotuner of the recursion schedule (no counterpart in the paper, which tunes
  * by hand for one machine): times pluq_modp on copies of A (device, m x n, row
  * stride lda, read only) under candidate schedules - leaf cut-off 1024, 512,
- * 2048 crossed with leaf kind per-leaf choice, barrier, wavefront (fork depth
- * 2), then fork depth 0, 1, 3 for the best - one warm run and the best of two
+ * 2048 crossed with leaf kind per-leaf choice, barrier, wavefront, cluster
+ * (fork depth 2), then fork depth 0, 1, 3 for the best - one warm run and the best of two
  * timed runs each, stopping once budget_ms (0: 10 s) is spent after at least
  * one schedule.  The fastest is stored in the context for (p, m, n, form) and
  * applied by later pluq_modp / echelon_modp / rank_profile_modp calls of that

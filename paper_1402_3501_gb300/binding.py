@@ -177,7 +177,7 @@ class Context:
                          "bytes": by.value, "tensor_flops": tf.value}
         return out
 
-    LEAF_KINDS = {0: "barrier", 1: "wavefront", 2: "per-leaf"}
+    LEAF_KINDS = {0: "barrier", 1: "wavefront", 2: "per-leaf", 3: "cluster"}
 
     def autotune(self, A: torch.Tensor, p: int, form="limb", budget_ms: float = 0.0,
                  stream=None) -> dict:

@@ -135,7 +135,8 @@ struct pluq_ctx {
   int bm = 128, bn = 128;  // base-case tile
   int trsm_block = 64;     // diagonal block of the triangular solves
   int leaf_dim = 1024;     // cooperative leaves up to leaf_dim x leaf_dim (0: off)
-  int leaf_kind = 2;       // 0: grid barrier per pivot, 1: wavefront, 2: chosen per leaf
+  int leaf_kind = 2;       // 0: grid barrier per pivot, 1: wavefront, 2: chosen per leaf,
+                           // 3: cluster barrier per pivot
   double leaf_density = 1.0;  // rank / min(m, n) of the last leaf of the current call
   int chain_rows = 0;      // rows per CTA of wavefront leaves (0: default)
   int64_t mmax = 0, nmax = 0;
@@ -209,6 +210,9 @@ int leaf_fits(pluq_ctx* c, int64_t m, int64_t n);
 int launch_leaf_chain(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
                       int32_t* perm_c, int32_t* rank_out);
 int chain_fits(pluq_ctx* c, int64_t m, int64_t n);
+int launch_leaf_cluster(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
+                        int32_t* perm_c, int32_t* rank_out);
+int cluster_leaf_fits(pluq_ctx* c, int64_t m, int64_t n);
 int leaf_max_dim();
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
 int batched_max_dim();

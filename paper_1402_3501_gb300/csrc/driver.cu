@@ -462,16 +462,21 @@ struct Recursion {
       PLUQ_TRY(launch_iota_pair(c, pr, m, pc, n));
       return PLUQ_OK;
     }
-    // wavefront leaves win on dense blocks, barrier leaves on rank-deficient
-    // ones; kind 2 guesses from the rank density of the previous leaf
+    // wavefront leaves win on dense blocks, cluster (else barrier) leaves on
+    // rank-deficient ones; kind 2 guesses from the rank density of the
+    // previous leaf
     const bool want_chain =
         c->leaf_kind == 1 || (c->leaf_kind == 2 && c->leaf_density > 0.5);
     const bool chain = c->leaf_dim > 0 && want_chain && chain_fits(c, m, n);
-    const bool leaf = !chain && c->leaf_dim > 0 && leaf_fits(c, m, n);
-    if (chain || leaf || (m <= c->bm && n <= c->bn)) {
+    const bool cluster = !chain && c->leaf_dim > 0 && (c->leaf_kind == 3 || c->leaf_kind == 2) &&
+                         cluster_leaf_fits(c, m, n);
+    const bool leaf = !chain && !cluster && c->leaf_dim > 0 && leaf_fits(c, m, n);
+    if (chain || cluster || leaf || (m <= c->bm && n <= c->bn)) {
       c->n_base++;
       if (chain)
         PLUQ_TRY(launch_leaf_chain(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      else if (cluster)
+        PLUQ_TRY(launch_leaf_cluster(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
       else if (leaf)
         PLUQ_TRY(launch_leaf_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
       else
@@ -482,7 +487,7 @@ struct Recursion {
       PLUQ_CUDA(cudaStreamSynchronize(c->stream));
       if (c->host_small[16] != 0) return c->host_small[16];
       *r_out = c->host_small[8];
-      if (chain || leaf) c->leaf_density = (double)*r_out / (double)std::min(m, n);
+      if (chain || cluster || leaf) c->leaf_density = (double)*r_out / (double)std::min(m, n);
       return PLUQ_OK;
     }
     if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
@@ -1115,7 +1120,7 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
       c->leaf_dim = value;
       return PLUQ_OK;
     case PLUQ_OPT_LEAF_KIND:
-      if (value < 0 || value > 2) return PLUQ_ERR_INVALID_ARG;
+      if (value < 0 || value > 3) return PLUQ_ERR_INVALID_ARG;
       c->leaf_kind = value;
       return PLUQ_OK;
     case PLUQ_OPT_TILE_M:
@@ -1213,7 +1218,7 @@ int pluq_autotune(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t*
   int st = PLUQ_OK;
   // stage 1: cut-off and leaf kind (the default schedule first); stage 2: fork depth
   for (int l : leaves) {
-    for (int k : {2, 0, 1}) {
+    for (int k : {2, 0, 1, 3}) {
       if (b_ms < 1e30 && spent() > budget_ms) break;
       double ms = 0;
       st = trial(l, k, 2, &ms);

@@ -192,7 +192,7 @@ SHAPES = [(1, 1), (1, 40), (40, 1), (17, 33), (128, 128), (129, 130), (200, 300)
           (513, 257)]
 
 
-@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 2), (0, 0)])
+@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 2), (1024, 3), (0, 0)])
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("p", [2, 3, 65521, 131071])
 @pytest.mark.parametrize("shape", SHAPES)
@@ -203,7 +203,8 @@ def test_pluq_uniform(ctx, leaf, form, p, shape):
         assert_parity(ctx, A, p, form)
 
 
-@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (96, 1), (96, 0), (96, 2), (0, 0)])
+@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 3), (96, 1), (96, 0), (96, 2),
+                                  (96, 3), (0, 0)])
 @pytest.mark.parametrize("p", [3, 131071])
 @pytest.mark.parametrize("shape", [(64, 64), (150, 200), (300, 260), (513, 257), (700, 700)])
 @pytest.mark.parametrize("frac", [0.0, 0.1, 0.5, 0.9])
@@ -244,7 +245,7 @@ def test_pluq_thin_gemm_switch(ctx, thin):
 
 
 @pytest.mark.parametrize("fork_depth", [0, 1, 4])
-@pytest.mark.parametrize("leaf", [(96, 0), (96, 1), (0, 0)])
+@pytest.mark.parametrize("leaf", [(96, 0), (96, 1), (96, 3), (0, 0)])
 @pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
                                           (65521, (600, 450), 1.0)])
 def test_pluq_concurrent_branches(ctx, fork_depth, leaf, p, shape, frac):
@@ -279,7 +280,8 @@ def test_pluq_leaf_too_large_for_child_context(ctx):
 @pytest.mark.parametrize("mode", [(0, (8, 8)), (0, (16, 8)), (0, (5, 13)), (0, (32, 32)),
                                   (0, (128, 64)), ((9, 0), (8, 8)), ((24, 0), (8, 8)),
                                   ((40, 0), (8, 8)), ((9, 1), (8, 8)), ((24, 1), (8, 8)),
-                                  ((40, 1), (8, 8)), ((1, 1), (8, 8))])
+                                  ((40, 1), (8, 8)), ((1, 1), (8, 8)), ((9, 3), (8, 8)),
+                                  ((40, 3), (8, 8))])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_pluq_deep_recursion(ctx, mode, seed):
     # small leaves / base tiles drive many recursion levels through every block step
@@ -290,6 +292,27 @@ def test_pluq_deep_recursion(ctx, mode, seed):
             assert_parity(ctx, g.A, p)
         A = workloads.uniform_matrix(77, 91, 5, seed)
         assert_parity(ctx, A, 5)
+
+
+# cluster leaves: 16-bit storage (p < 2^16), 16 + 8-bit planes (p < 2^24) and
+# 32-bit words, from a single row to the 1024 x 1024 limit, fewer rows than
+# CTAs, zero and full rank
+@pytest.mark.parametrize("p", [2, 3, 65521, 131071, 1048573, 2147483647])
+@pytest.mark.parametrize("shape,frac", [((1024, 1024), 1.0), ((1024, 1024), 0.06),
+                                        ((1000, 1024), 0.5), ((1024, 600), 0.3),
+                                        ((700, 700), 0.9), ((15, 1024), 1.0), ((1, 1024), 1.0),
+                                        ((1024, 1), 1.0), ((300, 300), 0.0), ((513, 1000), 1.0)])
+def test_pluq_cluster_leaf(ctx, p, shape, frac):
+    m, n = shape
+    r = int(frac * min(m, n))
+    if frac == 1.0:
+        A = workloads.uniform_matrix(m, n, p, 7)
+    else:
+        A = workloads.prescribed_rank_matrix(m, n, r, p, 7).A
+    with leaf_mode(ctx, (1024, 3)):
+        got = assert_parity(ctx, A, p, "limb")
+    if frac < 1.0:
+        assert got == r
 
 
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
@@ -623,7 +646,7 @@ def test_autotune_schedule_parity(ctx, p, shape, frac):
     torch.cuda.synchronize()
     assert torch.equal(Ad, keep)  # the tuner works on copies
     assert ch["leaf_dim"] in (512, 1024, 2048)
-    assert ch["leaf_kind"] in ("barrier", "wavefront", "per-leaf")
+    assert ch["leaf_kind"] in ("barrier", "wavefront", "per-leaf", "cluster")
     assert ch["fork_depth"] in (0, 1, 2, 3) and ch["ms"] > 0
     try:
         assert assert_parity(ctx, A, p, "limb") == r
