@@ -35,9 +35,9 @@ METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-e
 
 # DRAM traffic (read + write bytes) per launch of each kernel class from the
 # committed ncu captures (profiles/); None where no capture of the current kernel
-# exists.  The leaf figure is the mean over three leaf launches of this workload
-# (blocks of about 1000 x 1000; writes stay in L2 until evicted).
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 3.49e6}
+# exists.  The leaf figure is the mean over three cluster-leaf launches of this
+# workload (blocks of about 1000 x 1000; writes stay in L2 until evicted).
+NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 2.73e6}
 
 
 def field_ops(m: int, n: int, r: int) -> float:
