@@ -316,6 +316,9 @@ def bench_ours(args, world, rank, local):
     # schedule chosen by the library's autotuner on this matrix (untimed), then
     # warm-up (not timed) and bit-exact validation against the construction
     schedule = None
+    if args.decomposition == "iterative":
+        ctx.set_option("decomposition", 1)
+        ctx.set_option("slab_rows", args.slab_rows)
     if args.schedule:
         leaf, kind, fork = (int(x) for x in args.schedule.split(","))
         ctx.set_option("leaf_dim", leaf)
@@ -438,6 +441,9 @@ def bench_ours(args, world, rank, local):
                        "l2": "inputs (268 MB) larger than L2 (129 MB), no flush",
                        "step": "restore input (D2D copy) + pluq_modp",
                        "schedule": schedule or "default (leaf 1024, per-leaf kind, fork depth 2)",
+                       "decomposition": ("tile recursive" if args.decomposition == "recursive"
+                                         else f"tiled iterative (slab rows "
+                                              f"{args.slab_rows or 'leaf cut-off'})"),
                        "parallelism": f"replicas x{world}"},
             "bitexact": exact,
             "fgemm_dtype": "f16 digits, f32 accumulate" if form != "fp64" else "f64",
@@ -473,7 +479,12 @@ def main():
     ap.add_argument("--tune-budget-ms", type=float, default=15000.0)
     ap.add_argument("--schedule", default="",
                     help="leaf_dim,leaf_kind,fork_depth to time instead of autotuning "
-                         "(leaf kind 0 barrier, 1 wavefront, 2 per leaf)")
+                         "(leaf kind 0 barrier, 1 wavefront, 2 per leaf, 3 cluster)")
+    ap.add_argument("--decomposition", choices=["recursive", "iterative"], default="recursive",
+                    help="tile recursive (default) or tiled iterative (row slabs by column "
+                         "tiles), the paper's two rank-deficient eliminations")
+    ap.add_argument("--slab-rows", type=int, default=0,
+                    help="rows of a tiled-iterative slab (0: the leaf cut-off)")
     ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS),
                     help="matrix to factor (the default is the measured workload; the "
                          "others serve as small profiling cases)")

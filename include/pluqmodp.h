@@ -240,6 +240,19 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        64-bit sums, one reduction per entry) instead of
  *                        packing digits for the tensor cores; 0: every update
  *                        on the tensor cores.
+ *   PLUQ_OPT_DECOMPOSITION  [0, 1]: 0 (default) tile recursive (Sec. 4.1,
+ *                        "Tiled recursive elimination": both dimensions
+ *                        halved, F and G independent); 1 tiled iterative
+ *                        (Sec. 4.1, "Tiled iterative elimination" and the
+ *                        panel PLUQ figure): the first SLAB_ROWS rows are
+ *                        factored across all columns, by column tiles of the
+ *                        leaf cut-off taken in turn, then the Schur
+ *                        complement below them the same way.  Both give the
+ *                        same rank, rank profiles and rank profile matrix
+ *                        (the pivoting of the recursion recovers them for any
+ *                        split); P, Q and L\U may differ (any valid factors).
+ *   PLUQ_OPT_SLAB_ROWS   rows of a tiled-iterative slab [0, 2^31); 0
+ *                        (default): the leaf cut-off
  *   PLUQ_OPT_USE_TUNED   1 (default): factorizations whose (p, m, n, form)
  *                        was autotuned use the tuned schedule in place of
  *                        LEAF_DIM, LEAF_KIND and FORK_DEPTH; 0: ignore it.
@@ -253,6 +266,8 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_FORK_DEPTH 7
 #define PLUQ_OPT_USE_TUNED 8
 #define PLUQ_OPT_THIN_GEMM 9
+#define PLUQ_OPT_DECOMPOSITION 10
+#define PLUQ_OPT_SLAB_ROWS 11
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

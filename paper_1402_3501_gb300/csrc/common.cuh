@@ -92,8 +92,9 @@ struct DevBuf {
   T* as() const { return reinterpret_cast<T*>(ptr); }
 };
 
-// Upper bound on the recursion depth of the tile-recursive driver (each level
-// halves at least one dimension, and dimensions are < 2^31).
+// Index-vector slots of the tile-recursive driver (each level halves at least
+// one dimension, and dimensions are < 2^31); the tiled-iterative schedule,
+// whose depth grows with the number of slabs and tiles, sizes its own.
 constexpr int kMaxDepth = 72;
 
 // Kernel classes for the per-class CUDA-event timers.
@@ -143,7 +144,8 @@ struct pluq_ctx {
   // workspace
   DevBuf scratch;          // uint32 gathers, packed GEMM operands
   DevBuf pack;             // packed limb / fp64 GEMM operands
-  DevBuf perm_r, perm_c;   // int32 [kMaxDepth][mmax], [kMaxDepth][nmax]
+  DevBuf perm_r, perm_c;   // int32 [depth_slots][mmax], [depth_slots][nmax]
+  int depth_slots = kMaxDepth;  // recursion levels + one spare slot
   DevBuf tmp_i;            // int32 scratch for segment permutations
   DevBuf tri_inv;          // inverted diagonal blocks of a triangular solve
   DevBuf small;            // int32 / int64 scalars (rank, flags)
@@ -171,6 +173,11 @@ struct pluq_ctx {
   // read-only) and cooperative leaves in a child use at most its sm_count
   int fork_depth = 2;             // levels of the recursion that run F and G concurrently
   int thin_gemm = 1;              // limb form: CUDA-core fgemm for K <= kThinMaxK
+  // decomposition: 0 tile recursive (both dimensions halved); 1 tiled
+  // iterative (row slabs of slab_rows rows of the Schur complement in turn,
+  // each slab by column tiles of the leaf cut-off)
+  int decomposition = 0;
+  int slab_rows = 0;              // 0: the leaf cut-off
   int lane_depth = 0;             // 0 for the user's context
   pluq_ctx* parent = nullptr;
   pluq_ctx* lane[2] = {nullptr, nullptr};

@@ -305,6 +305,9 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->chain_rows = c->chain_rows;
   l->fork_depth = c->fork_depth;
   l->thin_gemm = c->thin_gemm;
+  l->decomposition = c->decomposition;
+  l->slab_rows = c->slab_rows;
+  l->depth_slots = c->depth_slots;
   l->mmax = c->mmax;
   l->nmax = c->nmax;
   l->limb_plan_p = c->limb_plan_p;
@@ -348,6 +351,7 @@ struct Recursion {
   int64_t lda;
   int32_t* rank_slot;  // device int32
   int32_t* PR(int d) { return c->perm_r.as<int32_t>() + (int64_t)d * c->mmax; }
+  int spare() const { return c->depth_slots - 1; }
   int32_t* PC(int d) { return c->perm_c.as<int32_t>() + (int64_t)d * c->nmax; }
   uint32_t* X(int64_t R0, int64_t C0, int64_t i, int64_t j) {
     return A + (R0 + i) * lda + (C0 + j);
@@ -490,7 +494,7 @@ struct Recursion {
       if (chain || cluster || leaf) c->leaf_density = (double)*r_out / (double)std::min(m, n);
       return PLUQ_OK;
     }
-    if (d + 2 >= kMaxDepth) return PLUQ_ERR_INVALID_ARG;  // slot kMaxDepth-1 is scratch
+    if (d + 2 >= c->depth_slots) return PLUQ_ERR_INVALID_ARG;  // the last slot is scratch
     c->n_nodes++;
     int64_t lim_m = c->leaf_dim > 0 ? c->leaf_dim : c->bm;
     int64_t lim_n = c->leaf_dim > 0 ? c->leaf_dim : c->bn;
@@ -500,8 +504,25 @@ struct Recursion {
       lim_m = std::max<int64_t>(1, m / 2);
       lim_n = std::max<int64_t>(1, n / 2);
     }
-    const int64_t m1 = m > lim_m ? split(m) : m;
-    const int64_t n1 = n > lim_n ? split(n) : n;
+    int64_t m1 = m > lim_m ? split(m) : m;
+    int64_t n1 = n > lim_n ? split(n) : n;
+    if (c->decomposition == 1 && (m > lim_m || n > lim_n)) {
+      // tiled iterative (Sec. 4.1): a slab of the first rows across all
+      // columns (A2, A4 empty: then G, the rows below, is the next step), and
+      // within a slab a tile of the first columns (A3, A4 empty: F, the
+      // columns right of it, is next)
+      const int64_t b = c->slab_rows > 0 ? c->slab_rows : lim_m;
+      if (m > b) {
+        m1 = b;
+        n1 = n;
+      } else if (n > lim_n) {
+        m1 = m;
+        n1 = lim_n;
+      } else {
+        m1 = lim_m;
+        n1 = n;
+      }
+    }
     const int64_t m2 = m - m1, n2 = n - n1;
     int32_t* cr = PR(d + 1);
     int32_t* cc = PC(d + 1);
@@ -574,7 +595,7 @@ struct Recursion {
                            cc + C0 + n1 + r2));
 
     // block-cyclic shifts
-    int32_t* tmp = PR(kMaxDepth - 1) + R0;  // spare row slot (this block's range)
+    int32_t* tmp = PR(spare()) + R0;  // spare row slot (this block's range)
     {
       const int64_t a = r1 + r2, fr = m1 - r1 - r2, gr = r3 + r4;
       if (fr > 0 && gr > 0) {
@@ -589,7 +610,7 @@ struct Recursion {
       const int64_t gn = n1 - r1 - r3;
       const bool ident = (r2 == 0 || (r3 == 0 && gn == 0)) && (r4 == 0 || gn == 0);
       if (!ident) {
-        int32_t* tmpc = PC(kMaxDepth - 1) + C0;
+        int32_t* tmpc = PC(spare()) + C0;
         const int64_t st[4] = {r3 + gn, 0, r3 + gn + r2, r3};
         const int64_t ln[4] = {r2, r3, r4, gn};
         const int64_t len = r3 + gn + r2 + r4;
@@ -647,15 +668,25 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
   TunedScope tuned(c, m, n);
   c->mmax = std::max<int64_t>(m, 1);
   c->nmax = std::max<int64_t>(n, 1);
-  PLUQ_TRY(c->perm_r.ensure(sizeof(int32_t) * kMaxDepth * c->mmax));
-  PLUQ_TRY(c->perm_c.ensure(sizeof(int32_t) * kMaxDepth * c->nmax));
+  // index-vector slots: one a recursion level.  Tiled iteration nests one
+  // level a slab and a tile (plus halvings of blocks no leaf takes)
+  const int64_t lim = std::max(1, c->leaf_dim > 0 ? c->leaf_dim : std::min(c->bm, c->bn));
+  const int64_t slab = c->slab_rows > 0 ? c->slab_rows : lim;
+  c->depth_slots = c->decomposition == 1
+                       ? (int)std::max<int64_t>(kMaxDepth, cdiv(m, slab) + cdiv(n, lim) +
+                                                               cdiv(slab, lim) + 72)
+                       : kMaxDepth;
+  PLUQ_TRY(c->perm_r.ensure(sizeof(int32_t) * c->depth_slots * c->mmax));
+  PLUQ_TRY(c->perm_c.ensure(sizeof(int32_t) * c->depth_slots * c->nmax));
   PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * std::max<int64_t>(m * n, 1)));
   PLUQ_TRY(c->tmp_i.ensure(sizeof(int32_t) * std::max(c->mmax, c->nmax)));
   PLUQ_TRY(c->small.ensure(256));
   PLUQ_TRY(ensure_inv_table(c));
   if (c->form == PLUQ_FORM_LIMB_F16) {
-    // digit planes of the largest fgemm operands (K <= min(m, n) / 2 + 64)
-    const int64_t kp = cdiv(std::min(m, n) / 2 + 64, 64) * 64;
+    // digit planes of the largest fgemm operands (K <= min(m, n) / 2 + 64; a
+    // tiled-iterative slab can give K up to its row count)
+    const int64_t kmax = c->decomposition == 1 ? std::min(std::min(m, n), slab) : 0;
+    const int64_t kp = cdiv(std::max(std::min(m, n) / 2, kmax) + 64, 64) * 64;
     const int64_t rows = cdiv(m, 128) * 128 + cdiv(n, 128) * 128;
     PLUQ_TRY(c->pack.ensure(sizeof(uint16_t) * 2 * rows * kp + 4096));
   }
@@ -1138,6 +1169,14 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_THIN_GEMM:
       if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;
       c->thin_gemm = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_DECOMPOSITION:
+      if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;
+      c->decomposition = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_SLAB_ROWS:
+      if (value < 0) return PLUQ_ERR_INVALID_ARG;
+      c->slab_rows = value;
       return PLUQ_OK;
     case PLUQ_OPT_USE_TUNED:
       if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;

@@ -315,6 +315,48 @@ def test_pluq_cluster_leaf(ctx, p, shape, frac):
         assert got == r
 
 
+# tiled-iterative decomposition (row slabs, each by column tiles): the same
+# rank, profiles and RPM as the oracle, valid factors; slabs of the leaf
+# cut-off and other heights, several leaf kinds, rank-deficient and full rank
+@pytest.mark.parametrize("slab", [0, 40, 150, 300])
+@pytest.mark.parametrize("leaf", [(96, 3), (96, 0), (96, 1), (0, 0)])
+@pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
+                                          (65521, (600, 450), 1.0), (131071, (450, 600), 0.1),
+                                          (2147483647, (300, 260), 0.7)])
+def test_pluq_tiled_iterative(ctx, slab, leaf, p, shape, frac):
+    m, n = shape
+    r = int(frac * min(m, n))
+    A = workloads.prescribed_rank_matrix(m, n, r, p, 11).A
+    ctx.set_option("decomposition", 1)
+    ctx.set_option("slab_rows", slab)
+    try:
+        with leaf_mode(ctx, leaf, tiles=(64, 64)):
+            assert assert_parity(ctx, A, p, "limb") == r
+    finally:
+        ctx.set_option("decomposition", 0)
+        ctx.set_option("slab_rows", 0)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pluq_tiled_iterative_bench_shape(ctx, form):
+    """The 8192 x 8192 rank-4096 workload under tiled iteration (slabs and tiles
+    of the leaf cut-off): rank, profiles and RPM as constructed, factors checked
+    by Freivalds' test."""
+    cfg = workloads.CONFIGS["lru-8192-r4096-p131071"]
+    g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, 1, device="cuda")
+    ctx.set_option("decomposition", 1)
+    try:
+        r, P, Q, LU, rrp, crp = run_pluq(ctx, g.A, cfg.p, form)
+    finally:
+        ctx.set_option("decomposition", 0)
+    assert r == g.rank
+    check_rpm_from_pq(P, Q, r, g.rpm)
+    assert rrp.tolist() == g.rrp.tolist() and crp.tolist() == g.crp.tolist()
+    assert not np.any(LU[r:, r:])
+    assert np.all(np.diag(LU[:r, :r]) != 0)
+    freivalds(g.A, cfg.p, P, Q, LU, r)
+
+
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
 def test_pluq_trsm_blocks(ctx, tb):
     p = 65521
