@@ -39,3 +39,15 @@ def test_status_codes_match_binding():
     text = open(os.path.join(ROOT, "include", "pluqmodp.h")).read()
     codes = {int(v): k for k, v in re.findall(r"#define (PLUQ_(?:OK|ERR_\w+))\s+(-?\d+)", text)}
     assert set(codes) == set(binding.STATUS)
+
+
+def test_options_match_binding():
+    """Every PLUQ_OPT_* code of the header has the binding's name for it, and the
+    binding names no option the header lacks; leaf kinds cover the documented range."""
+    from paper_1402_3501_gb300 import binding
+    text = open(os.path.join(ROOT, "include", "pluqmodp.h")).read()
+    opts = {k.lower(): int(v) for k, v in re.findall(r"#define PLUQ_OPT_(\w+)\s+(\d+)", text)}
+    assert opts == binding.Context.OPTIONS
+    lo, hi = (int(x) for x in re.search(r"PLUQ_OPT_LEAF_KIND\s+leaf kernel \[(\d+), (\d+)\]",
+                                        text).groups())
+    assert sorted(binding.Context.LEAF_KINDS) == list(range(lo, hi + 1))
