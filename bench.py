@@ -40,6 +40,26 @@ METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-e
 NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 2.73e6}
 
 
+def class_rooflines(classes: dict, peaks: dict) -> dict:
+    """Per kernel class of the profiled pass: launches, device ms, achieved HBM
+    bandwidth from its algorithmic bytes (and its fraction of the measured copy
+    bandwidth), and for the fgemm class its tensor rate and fraction of the
+    measured sustained bf16 peak (the fp16 dense rate equals the bf16 rate)."""
+    out = {}
+    for k, v in classes.items():
+        e = {"launches": v["launches"], "ms": round(v["ms"], 3)}
+        if v["ms"] > 0 and v["bytes"] > 0:
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            e["hbm_gbs"] = round(gbs, 1)
+            e["hbm_frac"] = round(gbs / peaks["hbm_gbs"], 4)
+        if v["ms"] > 0 and v.get("tensor_flops", 0) > 0:
+            tf = v["tensor_flops"] / (v["ms"] / 1e3) / 1e12
+            e["tensor_tflops"] = round(tf, 1)
+            e["tensor_frac"] = round(tf / peaks["bf16_sustained"], 4)
+        out[k] = e
+    return out
+
+
 def field_ops(m: int, n: int, r: int) -> float:
     return 2.0 * m * n * r - (m + n) * r * r + 2.0 * r ** 3 / 3.0
 
@@ -453,8 +473,7 @@ def bench_ours(args, world, rank, local):
                     "d2h_bytes_per_step": int(m * n * 4 + 4 * (m + n))},
             "gpu_launches": int(launches),
             "roofline": roof,
-            "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
-                               for k, v in classes.items()},
+            "kernel_classes": class_rooflines(classes, peaks),
             "profiled_pass_ms_per_step": round(ms_profiled, 3),
             "clocks": clocks,
             "wall_s_timed": round(wall, 3),
