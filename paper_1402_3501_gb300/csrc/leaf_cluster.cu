@@ -8,15 +8,17 @@
 // with one hardware cluster barrier instead of a grid barrier in global
 // memory: every CTA leaves its candidate (its first row with a live column,
 // that column and the inverse of the entry there) in its own shared memory;
-// after the barrier every CTA reads the G candidates and then the elected
-// row's entries in its columns straight from the other CTAs' shared memory
+// after the barrier every CTA reads the G candidates, then copies the elected
+// row right of its pivot column from the winner's shared memory into its own
 // (distributed shared memory), with no L2 round trip on the way.
 //
 // Storage per residue: 16 bits for p < 2^16, a 16-bit and an 8-bit plane for
 // p < 2^24, else 32 bits, so that a 1024 x 1024 block fits the shared memory
 // of 16 SMs for p < 2^24 (n <= 1024: thread tid of 1024 copies column tid of
-// the elected row; the elimination runs over work items of a few active rows
-// by a column chunk, one warp each).
+// the elected row).  The row updates run over work items of 4 active rows by
+// 64 columns, one warp each, with Shoup's precomputed-quotient products; the
+// first live column of an updated row is found afterwards, inside the first
+// 64-column chunk the update left non-zero (a per-row chunk mask).
 //
 // There is no wait on a memory word: the cluster barrier is a hardware barrier
 // and every CTA passes it the same number of times (the loop ends on the
@@ -137,8 +139,9 @@ __host__ __device__ inline ClLayout cl_layout(int m, int n, int G, int store) {
 // (V. Shoup, NTL's MulModPrecon): c' = floor(c 2^32 / p); for any 32-bit x,
 // q = floor(x c' / 2^32) is floor(x c / p) or one less, so x c - q p lies in
 // [0, 2p) and is exact in 32-bit wrap-around arithmetic (p < 2^31).
-// c' from pinv64 = floor(2^64 / p): the estimate floor(c 2^32 pinv64 / 2^64)
-// is c' or c' - 1, fixed by one comparison.
+// c' from pinv64 = floor((2^64 - 1) / p), which is within one of 2^64 / p:
+// the estimate floor(c 2^32 pinv64 / 2^64) is c' or c' - 1, fixed by one
+// comparison.
 __device__ __forceinline__ uint32_t shoup_pre(uint32_t c, uint32_t p, uint64_t pinv64) {
   const uint64_t x = (uint64_t)c << 32;
   uint64_t e = __umul64hi(x, pinv64);
@@ -561,7 +564,7 @@ int launch_leaf_cluster(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int
   cfg.numAttrs = 1;
   const uint32_t* tab = inv_table_ptr(c);
   const FieldP F = c->F;
-  const uint64_t pinv64 = ~0ull / F.p;  // floor(2^64 / p): p is not a power of two above 2
+  const uint64_t pinv64 = ~0ull / F.p;  // floor((2^64 - 1) / p)
   ProfScope ps(c, PC_BASE, 0, 8.0 * m * n);
   if (store == 0)
     PLUQ_CUDA(cudaLaunchKernelEx(&cfg, k_leaf_cluster<0>, X, ldx, m, n, F, pinv64, tab, perm_r,
