@@ -60,6 +60,14 @@ def class_rooflines(classes: dict, peaks: dict) -> dict:
     return out
 
 
+def clock_log_path(rank: int) -> str:
+    """Where the raw nvidia-smi samples of the timed region go (their summary is in
+    the JSON line): BENCH_CLOCK_DIR if set, else the system's temporary directory."""
+    import tempfile
+    return os.path.join(os.environ.get("BENCH_CLOCK_DIR", tempfile.gettempdir()),
+                        f"bench_clocks_{rank}.csv")
+
+
 def field_ops(m: int, n: int, r: int) -> float:
     return 2.0 * m * n * r - (m + n) * r * r + 2.0 * r ** 3 / 3.0
 
@@ -255,8 +263,7 @@ def bench_batched(args, world, rank, local):
         Q = plan.Qs[b][:ns[b]].cpu().numpy()
         exact = exact and set(zip(P[:r].tolist(), Q[:r].tolist())) == gens[b].rpm
     ctx.profile(False)
-    sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp", f"bench_clocks_{rank}.csv"))
+    sampler = ClockSampler(local, clock_log_path(rank))
     ms_step = time_batched(plan, A, A0, args.steps, stream)
     clocks = sampler.stop()
     launches = sum(c["launches"] for c in ctx.profile_read().values())
@@ -367,8 +374,7 @@ def bench_ours(args, world, rank, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp", f"bench_clocks_{rank}.csv"))
+    sampler = ClockSampler(local, clock_log_path(rank))
     wall0 = time.time()
     ms = time_steps(pq, ctx, A, A0, p, form, args.steps, stream)
     wall = time.time() - wall0
