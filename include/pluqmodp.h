@@ -197,6 +197,26 @@ int rank_profile_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const in
                               int32_t* const* rrp, int32_t* const* crp, int64_t* ranks,
                               int32_t* status, int form, void* stream);
 
+/* Reduced row echelon form of every matrix of a batch (the batched form of
+ * echelon_modp, Sec. 4.1): each matrix is factored and solved in turn on the
+ * stream (each needs its own triangular solve by its own rank).
+ *   m, n, lda, ldr  host int64 arrays of length batch (lda[b], ldr[b] >= n[b]).
+ *   A        host array of batch device pointers, not modified.
+ *   R        host array of batch device pointers: min(m[b], n[b]) x n[b]; receive
+ *            the r x n RREF in their first r rows.
+ *   crp      host array of batch device pointers (the array or an entry may be
+ *            NULL): int32, length >= min(m[b], n[b]); receive the pivot columns.
+ *   ranks    host, batch entries; -1 for a matrix that failed.
+ *   status   host, batch entries (may be NULL): per-matrix status codes.
+ * Returns the first failing per-matrix status, else PLUQ_OK; a failure that is
+ * not the matrix's own (prime, form, workspace, device) stops the batch and
+ * marks the remaining matrices with it.  Each factorization synchronises the
+ * stream, as in echelon_modp. */
+int echelon_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const int64_t* m,
+                         const int64_t* n, const uint32_t* const* A, const int64_t* lda,
+                         uint32_t* const* R, const int64_t* ldr, int32_t* const* crp,
+                         int64_t* ranks, int32_t* status, int form, void* stream);
+
 /* Host copy of the rank found by the last factorization on this context. */
 int pluq_last_rank(pluq_ctx* ctx, int64_t* rank);
 

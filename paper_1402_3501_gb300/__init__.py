@@ -7,13 +7,15 @@ holds the CUDA sources (csrc/), the in-tree build (build.py) and the Python
 binding (binding.py).
 """
 from .binding import (BatchPlan, FORM_AUTO, FORM_FP64, FORM_LIMB_F16, Context, PluqError, PLUQResult,
-                      column_echelon_modp, default_context, echelon_modp, fgemm_modp,
+                      column_echelon_modp, default_context, echelon_modp, echelon_modp_batched,
+                      fgemm_modp,
                       fgemm_modp_noalloc, load, pluq_modp, pluq_modp_batched, rank_profile_modp,
                       rank_profile_modp_batched)
 
 __all__ = [
     "BatchPlan",
     "FORM_AUTO", "FORM_FP64", "FORM_LIMB_F16", "Context", "PluqError", "PLUQResult",
-    "column_echelon_modp", "default_context", "echelon_modp", "fgemm_modp", "fgemm_modp_noalloc",
+    "column_echelon_modp", "default_context", "echelon_modp", "echelon_modp_batched", "fgemm_modp",
+    "fgemm_modp_noalloc",
     "load", "pluq_modp", "pluq_modp_batched", "rank_profile_modp", "rank_profile_modp_batched",
 ]

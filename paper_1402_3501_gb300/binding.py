@@ -36,7 +36,7 @@ SYMBOLS = [
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
     "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
     "fgemm_modp_noalloc", "pluq_set_option", "pluq_autotune", "column_echelon_modp",
-    "rank_profile_modp_batched",
+    "rank_profile_modp_batched", "echelon_modp_batched",
 ]
 
 
@@ -399,6 +399,45 @@ def pluq_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None,
     if return_status:
         return outs + (list(status),)
     _check(st, "pluq_modp_batched")
+    return outs
+
+
+def echelon_modp_batched(As: list, p: int, form="auto", ctx: Context | None = None,
+                         stream=None, return_status: bool = False):
+    """Reduced row echelon forms of a list of CUDA int32 matrices (not modified):
+    (ranks, Rs (r x n each), crps[, status])."""
+    if not As:
+        return ([], [], [], []) if return_status else ([], [], [])
+    ctx = ctx or default_context(As[0].device.index)
+    b = len(As)
+    ms = (ctypes.c_int64 * b)()
+    ns = (ctypes.c_int64 * b)()
+    lds = (ctypes.c_int64 * b)()
+    ldr = (ctypes.c_int64 * b)()
+    aptr = (ctypes.c_void_p * b)()
+    rptr = (ctypes.c_void_p * b)()
+    cptr = (ctypes.c_void_p * b)()
+    ranks = (ctypes.c_int64 * b)()
+    status = (ctypes.c_int32 * b)()
+    Rs, Cs = [], []
+    for i, A in enumerate(As):
+        m, n, ld = _matrix_args(A)
+        ms[i], ns[i], lds[i], ldr[i] = m, n, ld, max(n, 1)
+        aptr[i] = A.data_ptr() if A.numel() else None
+        R = torch.zeros((max(min(m, n), 1), max(n, 1)), dtype=torch.int32, device=A.device)
+        cc = torch.empty(max(min(m, n), 1), dtype=torch.int32, device=A.device)
+        Rs.append(R)
+        Cs.append(cc)
+        rptr[i] = R.data_ptr()
+        cptr[i] = cc.data_ptr()
+    st = load().echelon_modp_batched(ctx.handle, p, b, ms, ns, aptr, lds, rptr, ldr, cptr, ranks,
+                                     status, _form(form), _stream_handle(stream))
+    rk = list(ranks)
+    outs = (rk, [Rs[i][:max(rk[i], 0), :ns[i]] for i in range(b)],
+            [Cs[i][:max(rk[i], 0)] for i in range(b)])
+    if return_status:
+        return outs + (list(status),)
+    _check(st, "echelon_modp_batched")
     return outs
 
 

@@ -877,9 +877,11 @@ int rank_profile_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint3
 // RREF of the m x n matrix W (workspace, ld ldw, factored in place) written
 // with strides (rs, cs); rank to rank_dev, pivot columns to crp (may be NULL).
 static int echelon_core(pluq_ctx* c, int64_t m, int64_t n, uint32_t* W, int64_t ldw, uint32_t* R,
-                        int64_t rs, int64_t cs, int64_t* rank_dev, int32_t* crp) {
+                        int64_t rs, int64_t cs, int64_t* rank_dev, int32_t* crp,
+                        int64_t* r_host = nullptr) {
   int64_t r = 0;
   PLUQ_TRY(factor(c, m, n, W, ldw, &r));
+  if (r_host) *r_host = r;
   PLUQ_TRY(write_outputs(c, m, n, r, nullptr, nullptr, rank_dev, nullptr, nullptr));
   if (r == 0) return PLUQ_OK;
   // X = U1^{-1} [U1 U2] in the Q frame: only U2 needs solving.
@@ -905,6 +907,48 @@ int echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* 
   PLUQ_TRY(copy_to_work(c, m, n, A, lda));
   return echelon_core(c, m, n, c->work.as<uint32_t>(), std::max<int64_t>(n, 1), R, ldr, 1,
                       rank_dev, crp);
+}
+
+int echelon_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m,
+                         const int64_t* n, const uint32_t* const* A, const int64_t* lda,
+                         uint32_t* const* R, const int64_t* ldr, int32_t* const* crp,
+                         int64_t* ranks, int32_t* status, int form, void* stream) {
+  if (!c || batch < 0 || (batch > 0 && (!m || !n || !A || !lda || !R || !ldr || !ranks)))
+    return PLUQ_ERR_INVALID_ARG;
+  // one matrix after the other on the stream: each needs its own triangular
+  // solve X2 = U1^{-1} U2 of its own rank, so the one-CTA-per-matrix kernel of
+  // the batched factorization does not carry over
+  int first_bad = PLUQ_OK;
+  for (int32_t b = 0; b < batch; ++b) {
+    int64_t r = 0;
+    int st = PLUQ_OK;
+    const bool argok = m[b] >= 0 && n[b] >= 0 &&
+                       (m[b] == 0 || n[b] == 0 ||
+                        (A[b] && R[b] && lda[b] >= n[b] && ldr[b] >= n[b]));
+    if (!argok) {
+      st = PLUQ_ERR_INVALID_ARG;
+    } else {
+      st = prepare(c, p, m[b], n[b], form, stream);
+      if (st == PLUQ_OK && m[b] > 0 && n[b] > 0) {
+        st = copy_to_work(c, m[b], n[b], A[b], lda[b]);
+        if (st == PLUQ_OK)
+          st = echelon_core(c, m[b], n[b], c->work.as<uint32_t>(), n[b], R[b], ldr[b], 1,
+                            nullptr, crp ? crp[b] : nullptr, &r);
+      }
+    }
+    ranks[b] = st == PLUQ_OK ? r : -1;
+    if (status) status[b] = st;
+    if (st != PLUQ_OK && first_bad == PLUQ_OK) first_bad = st;
+    if (st != PLUQ_OK && st != PLUQ_ERR_INVALID_ARG && st != PLUQ_ERR_ENTRY_OUT_OF_RANGE) {
+      // not a fault of this matrix (prime, form, workspace, device): stop here
+      for (int32_t e = b + 1; e < batch; ++e) {
+        ranks[e] = -1;
+        if (status) status[e] = st;
+      }
+      return st;
+    }
+  }
+  return first_bad;
 }
 
 int column_echelon_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t* A,

@@ -564,6 +564,30 @@ def test_rank_profile_batched(ctx, p):
         assert cc.cpu().tolist() == g.crp.tolist()
 
 
+@pytest.mark.parametrize("p", [2, 65521, 131071, 2147483647])
+def test_echelon_batched(ctx, p):
+    """Batched RREF equals the oracle's, matrix by matrix (rank, pivot columns and
+    the reduced rows), with an empty matrix and one whose entry is out of range
+    (its own status, the others unaffected)."""
+    shapes = [(40, 60, 20), (300, 257, 200), (33, 33, 33), (1, 7, 1), (700, 130, 52), (96, 128, 0)]
+    gens = [workloads.prescribed_rank_matrix(m, n, r, p, 50 + i) for i, (m, n, r) in
+            enumerate(shapes)]
+    As = [to_dev(g.A) for g in gens]
+    bad = np.zeros((8, 9), np.int64)
+    bad[3, 4] = p  # p <= 2^31 - 1: still an int32
+    As.insert(2, to_dev(bad))
+    As.append(torch.zeros((0, 5), dtype=torch.int32, device="cuda"))
+    ranks, Rs, crps, status = pq.echelon_modp_batched(As, p, ctx=ctx, return_status=True)
+    torch.cuda.synchronize()
+    assert status[2] == -4 and ranks[2] == -1  # PLUQ_ERR_ENTRY_OUT_OF_RANGE
+    assert status[-1] == 0 and ranks[-1] == 0
+    for i, g in zip([0, 1, 3, 4, 5, 6], gens):
+        rr, Rref = oracle.rref(g.A, p)
+        assert status[i] == 0 and ranks[i] == rr == g.rank
+        assert crps[i].cpu().tolist() == g.crp.tolist()
+        assert np.array_equal(Rs[i].cpu().numpy().astype(np.int64), Rref.astype(np.int64))
+
+
 def test_batched_bad_entry_status(ctx):
     p = 65521
     good = workloads.prescribed_rank_matrix(50, 60, 20, p, seed=1).A
