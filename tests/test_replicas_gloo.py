@@ -53,3 +53,44 @@ def test_two_replicas_gloo():
     assert res[0][1] == res[1][1] == 20.0
     F = 2 * 64 * 48 * 20 - (64 + 48) * 20 ** 2 + 2 * 20 ** 3 / 3
     assert np.isclose(res[0][2], world * F / 0.020 / 1e9)
+
+
+def _dead_replica_main(rank, world, port, out):
+    import sys
+    import time
+    from datetime import timedelta
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=10))
+    import bench
+    if rank == 1:
+        out[1] = "left"
+        os._exit(3)  # this replica dies between steps, before the timing reduction
+    t0 = time.time()
+    try:
+        bench.max_over_ranks(10.0, dist, "cpu")
+        out[0] = ("no error", time.time() - t0)
+    except Exception as e:  # the dead peer surfaces as an error on the host
+        out[0] = (type(e).__name__, time.time() - t0)
+
+
+def test_dead_replica_is_reported():
+    """A replica that leaves between steps: the surviving rank's timing reduction
+    ends with an error within the process-group timeout instead of hanging."""
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_dead_replica_main, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+        alive = [p.is_alive() for p in procs]
+        for p in procs:
+            if p.is_alive():
+                p.kill()
+        res = dict(out)
+    assert not any(alive)
+    assert procs[1].exitcode == 3 and res[1] == "left"
+    assert res[0][0] != "no error" and res[0][1] < 60
