@@ -490,6 +490,33 @@ def bench_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def profile_fgemm(args):
+    """One kernel-level case for ncu captures: C (M x N) -= A (M x K) B (K x N) mod p
+    through fgemm_modp, `--repeat` times on seeded uniform residues; prints one line
+    (not a bench line: nothing is checked here, the parity tests do that)."""
+    import torch
+    import paper_1402_3501_gb300 as pq
+    M, N, K = (int(x) for x in args.fgemm.lower().split("x"))
+    p = args.p
+    dev = lambda X: torch.from_numpy(X.astype(np.int32)).cuda()  # noqa: E731
+    A = dev(workloads.uniform_matrix(M, K, p, 1, "casea"))
+    B = dev(workloads.uniform_matrix(K, N, p, 1, "caseb"))
+    C = dev(workloads.uniform_matrix(M, N, p, 1, "casec"))
+    ctx = pq.Context(0)
+    form = "fp64" if args.form == "fp64" else "limb"
+    ms = []
+    for _ in range(max(1, args.repeat)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        pq.fgemm_modp(C, A, B, p, form=form, ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(f"fgemm {M}x{N}x{K} p={p} {form}: last {ms[-1]:.3f} ms "
+          f"({2.0 * M * N * K / ms[-1] / 1e9:.1f} field Tops/s)", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,10 +540,17 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS),
                     help="matrix to factor (the default is the measured workload; the "
                          "others serve as small profiling cases)")
+    ap.add_argument("--fgemm", default="",
+                    help="MxNxK: profiling case of one fgemm_modp call instead of the bench "
+                         "(with --p, --form, --repeat)")
+    ap.add_argument("--p", type=int, default=65521, help="prime of the --fgemm case")
+    ap.add_argument("--repeat", type=int, default=2, help="calls of the --fgemm case")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.fgemm:
+        profile_fgemm(args)
+    elif args.impl == "reference":
         bench_reference(args, world, rank)
     elif workloads.CONFIGS[args.workload].kind == "batched":
         bench_batched(args, world, rank, local)

@@ -137,7 +137,10 @@ int rank_profile_modp(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uin
  * and kernel-level checks.
  *   A  device, M x K, lda >= K;  B device, K x N, ldb >= N;
  *   C  device, M x N, ldc >= N, updated in place.  C may not overlap A or B.
- * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM, NO_WORKSPACE, CUDA. */
+ * The call reads the kernels' device error word back, so it returns once the
+ * product is complete on `stream`.
+ * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM, NO_WORKSPACE, CUDA, TIMEOUT (a
+ * bounded device wait ran out; C is then left unchanged or partly updated). */
 int fgemm_modp(pluq_ctx* ctx, uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
                int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc, int form,
                void* stream);
@@ -155,9 +158,13 @@ int fgemm_modp(pluq_ctx* ctx, uint32_t p, int64_t M, int64_t N, int64_t K, const
  *   The first call on a device looks up that array's device address (with
  *   the device current), so make it before any stream capture.  All calls
  *   share the array: calls that overlap on the GPU (other streams, other
- *   host threads) race; issue them on one stream.
+ *   host threads) race; issue them on one stream.  The call reads the
+ *   kernel's error word back into a host variable of its own (no
+ *   allocation), so it returns once the product is complete on `stream`.
  * Errors: INVALID_ARG, P_*, UNSUPPORTED_FORM (no limb plan; not reached for
- * p < 2^31), TOO_LARGE, CUDA. */
+ * p < 2^31), TOO_LARGE (also for any dimension beyond the array), CUDA,
+ * TIMEOUT (a bounded device wait ran out; C is then left unchanged or partly
+ * updated). */
 int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, const uint32_t* A,
                        int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc,
                        void* stream);

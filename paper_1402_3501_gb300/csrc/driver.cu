@@ -979,7 +979,12 @@ int fgemm_modp(pluq_ctx* c, uint32_t p, int64_t M, int64_t N, int64_t K, const u
   PLUQ_TRY(prepare(c, p, M, N, form, stream));
   PLUQ_TRY(c->small.ensure(256));
   PLUQ_CUDA(cudaMemsetAsync(c->small.ptr, 0, 256, c->stream));
-  return fgemm_sub(c, M, N, K, A, lda, B, ldb, C, ldc);
+  PLUQ_TRY(fgemm_sub(c, M, N, K, A, lda, B, ldb, C, ldc));
+  // the kernels' device error word (int 16): a bounded wait that ran out
+  PLUQ_CUDA(cudaMemcpyAsync(c->host_small + 16, c->small.as<int>() + 16, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, c->stream));
+  PLUQ_CUDA(cudaStreamSynchronize(c->stream));
+  return c->host_small[16] != 0 ? c->host_small[16] : PLUQ_OK;
 }
 
 int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, const int64_t* n,
@@ -1397,6 +1402,7 @@ const char* pluq_status_string(int s) {
     case PLUQ_ERR_NO_WORKSPACE: return "device workspace allocation failed";
     case PLUQ_ERR_CUDA: return "CUDA error";
     case PLUQ_ERR_TIMEOUT: return "device wait timed out";
+    case PLUQ_ERR_TOO_LARGE: return "problem exceeds the fixed scratch array";
     default: return "unknown status";
   }
 }

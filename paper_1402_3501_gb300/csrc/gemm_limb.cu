@@ -700,7 +700,9 @@ int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
 // stream capture.  Every call reuses the same array (the previous contents
 // remain; the packing pass rewrites every byte the kernel reads and the
 // error word is cleared on the call's stream), so calls that overlap on the
-// GPU - concurrent streams, or several host threads - race on it.
+// GPU - concurrent streams, or several host threads - race on it.  The call
+// reads the kernel's error word back (into a host variable on its own stack,
+// no allocation) and so returns once the product is complete.
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
@@ -750,7 +752,13 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
                 uint32_t* C, int64_t ldc, cudaStream_t s) {
   using Cfg = LimbCfg<L>;
   constexpr int TN = Cfg::TN;
+  // each dimension alone is checked against the array before any product of
+  // them is formed, so the byte counts below cannot wrap
+  const int64_t cap = (int64_t)(kNoAllocScratchBytes / sizeof(__half));
+  if (M > cap || N > cap || K > cap) return PLUQ_ERR_TOO_LARGE;
   const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, TN) * TN, Kp = cdiv(K, kTK) * kTK;
+  if (L * Mp > cap || L * Np > cap || Kp > cap) return PLUQ_ERR_TOO_LARGE;
+  if ((L * Mp + L * Np) > cap / Kp) return PLUQ_ERR_TOO_LARGE;
   const size_t abytes = sizeof(__half) * L * Mp * Kp, bbytes = sizeof(__half) * L * Np * Kp;
   const size_t aoff = ((abytes + 1023) / 1024) * 1024;
   if (aoff + bbytes > kNoAllocScratchBytes) return PLUQ_ERR_TOO_LARGE;
@@ -767,7 +775,12 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
                                                          (int)(Kp / kTK), pl.group_kb, C, ldc, F,
                                                          pl.bias, pl.bias_hi, d.err);
   PLUQ_CUDA(cudaGetLastError());
-  return PLUQ_OK;
+  // the kernel's error word (a bounded wait that ran out leaves C as it was)
+  // comes back to the host: the call returns once the product is done
+  int err = 0;
+  PLUQ_CUDA(cudaMemcpyAsync(&err, d.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PLUQ_CUDA(cudaStreamSynchronize(s));
+  return err != 0 ? err : PLUQ_OK;
 }
 
 }  // namespace
