@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 tile-recursive PLUQ over GF(p).
 
-Workload: one 8192 x 8192 matrix over GF(131071) of rank 4096 with random row
-and column rank profiles (A = L R U, Sec. 4.1 S16K-like shape), factored by
-pluq_modp (P, L, U, Q, rank, both rank profiles).  One step = restore the
+Workload: one 32768 x 32768 matrix over GF(65521) with entries i.i.d. uniform
+in [0, p) (full rank with high probability; the shape of the paper's dense
+experiments, Sec. 3 and Table 3, at the largest size one GPU holds), factored
+by pluq_modp (P, L, U, Q, rank, both rank profiles).  One step = restore the
 input in HBM + one full factorization.  Metric: effective Gfops =
-F(m, n, r) / t with F = 2mnr - (m+n)r^2 + 2r^3/3 field operations.
+F(m, n, r) / t with F = 2mnr - (m+n)r^2 + 2r^3/3 field operations.  The
+8192 x 8192 rank-4096 matrix over GF(131071) with random rank profiles (A = L R
+U, the S16K-like shape of Sec. 4.1) is timed as a second workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,14 +33,14 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-WORKLOAD = "lru-8192-r4096-p131071"
+WORKLOAD = "uniform-32768-p65521"
+SECOND_WORKLOAD = "lru-8192-r4096-p131071"
 METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-exact"
 
-# DRAM traffic (read + write bytes) per launch of each kernel class from the
-# committed ncu captures (profiles/); None where no capture of the current kernel
-# exists.  The leaf figure is the mean over three cluster-leaf launches of this
-# workload (blocks of about 1000 x 1000; writes stay in L2 until evicted).
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"base": 2.73e6}
+# DRAM traffic (read + write bytes) per launch of a kernel class on a workload,
+# from the committed ncu captures (profiles/); absent where no capture of the
+# current kernel exists.
+NCU_TRAFFIC_PER_LAUNCH: dict[tuple[str, str], float] = {}
 
 
 def class_rooflines(classes: dict, peaks: dict) -> dict:
@@ -66,6 +69,31 @@ def clock_log_path(rank: int) -> str:
     import tempfile
     return os.path.join(os.environ.get("BENCH_CLOCK_DIR", tempfile.gettempdir()),
                         f"bench_clocks_{rank}.csv")
+
+
+def golden_rpm(key: str, seed: int = 1):
+    """The oracle's rank profile matrix of a uniform workload, as stored under
+    tests/golden/ by its writer script (None when no such file exists)."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_rpm_{key}_seed{seed}.npz")
+    if not os.path.exists(path):
+        return None
+    d = np.load(path)
+    return {"rank": int(d["rank"][0]), "rpm": set(zip(d["piv_rows"].tolist(),
+                                                      d["piv_cols"].tolist())),
+            "rrp": d["rrp"].tolist(), "crp": d["crp"].tolist()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the platform's description."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def field_ops(m: int, n: int, r: int) -> float:
@@ -327,8 +355,8 @@ def bench_ours(args, world, rank, local):
     cfg = workloads.CONFIGS[args.workload]
     m, n, p = cfg.m, cfg.n, cfg.p
     if cfg.kind == "uniform":
-        # profiling case only: full rank with high probability, no construction to
-        # check against here (the parity tests compare it with the oracle)
+        # full rank with high probability; checked against the oracle's rank
+        # profile matrix where one is stored (tests/golden/)
         g = None
         A_host = workloads.uniform_matrix(m, n, p, seed=1)
     else:
@@ -361,12 +389,14 @@ def bench_ours(args, world, rank, local):
     torch.cuda.synchronize()
     r = res.rank
     exact = None
-    if g is not None:
+    want = ({"rank": g.rank, "rpm": g.rpm, "rrp": g.rrp.tolist(), "crp": g.crp.tolist()}
+            if g is not None else golden_rpm(args.workload))
+    if want is not None:
         P = res.P.cpu().numpy()
         Q = res.Q.cpu().numpy()
-        exact = (r == g.rank and set(zip(P[:r].tolist(), Q[:r].tolist())) == g.rpm
-                 and res.rrp.cpu().tolist() == g.rrp.tolist()
-                 and res.crp.cpu().tolist() == g.crp.tolist())
+        exact = (r == want["rank"] and set(zip(P[:r].tolist(), Q[:r].tolist())) == want["rpm"]
+                 and res.rrp.cpu().tolist() == want["rrp"]
+                 and res.crp.cpu().tolist() == want["crp"])
 
     # timed region: CUDA events on the launching stream around K steps; the
     # library counts its own kernel launches
@@ -395,10 +425,10 @@ def bench_ours(args, world, rank, local):
     # FP64-embedding form on the same input (the paper's representation)
     fp64 = None
     if not args.no_fp64:
-        for _ in range(1):
-            A.copy_(A0)
-            pq.pluq_modp(A, p, form="fp64", ctx=ctx)
-        ms64 = time_steps(pq, ctx, A, A0, p, "fp64", max(1, min(args.steps, 2)), stream)
+        A.copy_(A0)
+        pq.pluq_modp(A, p, form="fp64", ctx=ctx)
+        ms64 = time_steps(pq, ctx, A, A0, p, "fp64", max(1, min(args.steps, args.fp64_steps)),
+                          stream)
         ms64 = max_over_ranks(ms64, dist, "cuda")
         fp64 = {"value": round(whole_job_gfops(world, F, ms64), 3), "ms_per_step": round(ms64, 3)}
 
@@ -431,18 +461,23 @@ def bench_ours(args, world, rank, local):
     timed = c["launches"] if dom not in ("perm", "pack") else c["launches"] / 2
     avg_ms = c["ms"] / max(1, timed)
     if dom == "fgemm":
-        achieved = c["tensor_flops"] / (c["ms"] / 1e3) / 1e12
+        # algorithmic work = the field operations 2MNK of the Schur updates; the
+        # limb form issues L^2 digit products for each (L = 2 below p ~ 2^18)
+        achieved = c["flops"] / (c["ms"] / 1e3) / 1e12
+        issued = c["tensor_flops"] / (c["ms"] / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": round(achieved, 2),
                 "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
-                "peak_note": f"fp16 dense = bf16 rate; {peaks['source']} sustained bf16"}
+                "peak_note": f"fp16 dense = bf16 rate; {peaks['source']} sustained bf16",
+                "achieved_issued": round(issued, 2),
+                "frac_issued": round(issued / peaks["bf16_sustained"], 4),
+                "issued_note": "tensor flops actually issued (digit products, tile padding)"}
     else:
         achieved = c["bytes"] / (c["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "peak_note": f"{peaks['source']} HBM copy bandwidth"}
     roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
     roof["kernel_class"] = dom
-    # the committed captures are of the default workload's kernels
-    roof["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get(dom) if args.workload == WORKLOAD else None
+    roof["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get((args.workload, dom))
     roof["avg_launch_ms"] = round(avg_ms, 4)
 
     cpu = None
@@ -455,7 +490,13 @@ def bench_ours(args, world, rank, local):
         dt = time.time() - t
         assert rs_ is None or ref.rank == rs_
         cpu = {"value": round(field_ops(ms_, ns_, ref.rank) / dt / 1e9, 3), "unit": "Gfops",
-               "cores": cores, "kind": "oracle", "sample": f"{sample}, one run ({dt:.1f} s)"}
+               "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
+               "sample": f"{sample}, one run ({dt:.1f} s)"}
+
+    # the second workload (rank deficient, random rank profiles), same context
+    second = None
+    if not args.no_second and args.workload == WORKLOAD:
+        second = bench_second(pq, ctx, args, stream)
 
     if rank == 0:
         line = {
@@ -464,7 +505,7 @@ def bench_ours(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "p": p, "form": form,
-                       "l2": "inputs (268 MB) larger than L2 (129 MB), no flush",
+                       "l2": f"inputs ({m * n * 4 / 1e6:.0f} MB) larger than L2 (129 MB), no flush",
                        "step": "restore input (D2D copy) + pluq_modp",
                        "schedule": schedule or "default (leaf 1024, per-leaf kind, fork depth 2)",
                        "decomposition": ("tile recursive" if args.decomposition == "recursive"
@@ -484,10 +525,35 @@ def bench_ours(args, world, rank, local):
             "clocks": clocks,
             "wall_s_timed": round(wall, 3),
             "cpu_baseline": cpu,
+            "second_workload": second,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def bench_second(pq, ctx, args, stream) -> dict:
+    """The 8192 x 8192 rank-4096 workload on the same context: autotuned schedule,
+    warm-up, then timed steps, checked against its construction."""
+    import torch
+    cfg = workloads.CONFIGS[SECOND_WORKLOAD]
+    g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
+    A0 = torch.from_numpy(g.A.astype(np.int32)).cuda()
+    A = torch.empty_like(A0)
+    sched = ctx.autotune(A0, cfg.p, form=args.form, budget_ms=min(args.tune_budget_ms, 8000.0))
+    for _ in range(3):
+        A.copy_(A0)
+        res = pq.pluq_modp(A, cfg.p, form=args.form, ctx=ctx)
+    torch.cuda.synchronize()
+    r = res.rank
+    P, Q = res.P.cpu().numpy(), res.Q.cpu().numpy()
+    exact = (r == g.rank and set(zip(P[:r].tolist(), Q[:r].tolist())) == g.rpm
+             and res.rrp.cpu().tolist() == g.rrp.tolist()
+             and res.crp.cpu().tolist() == g.crp.tolist())
+    ms = time_steps(pq, ctx, A, A0, cfg.p, args.form, 10, stream)
+    return {"workload": SECOND_WORKLOAD, "value": round(field_ops(cfg.m, cfg.n, r) / ms / 1e6, 3),
+            "unit": "Gfops", "ms_per_step": round(ms, 3), "steps": 10, "bitexact": bool(exact),
+            "schedule": sched}
 
 
 def profile_fgemm(args):
@@ -525,6 +591,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", choices=["limb", "fp64", "auto"], default="limb")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the FP64-embedding form (after one untimed)")
+    ap.add_argument("--no-second", action="store_true",
+                    help="skip the second (8192^2 rank-4096) workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default schedule instead of the autotuned one")

@@ -235,6 +235,22 @@ __global__ void k_merge_err(int* dst, const int* src) {
   if (*src != 0 && *dst == 0) *dst = *src;
 }
 
+// flags[0] = (perm_r[i] == i for all i < m), flags[1] = (perm_c[j] == j for all
+// j < n): a leaf whose pivots fell on the diagonal leaves the blocks beside it
+// unpermuted, and the recursion skips those permutation launches.
+__global__ void k_perm_identity(const int32_t* __restrict__ perm_r, int m,
+                                const int32_t* __restrict__ perm_c, int n, int32_t* flags) {
+  int bad_r = 0, bad_c = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) bad_r |= perm_r[i] != i;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) bad_c |= perm_c[j] != j;
+  bad_r = __syncthreads_or(bad_r);
+  bad_c = __syncthreads_or(bad_c);
+  if (threadIdx.x == 0) {
+    flags[0] = !bad_r;
+    flags[1] = !bad_c;
+  }
+}
+
 dim3 grid2(int64_t rows, int64_t cols) {
   int64_t gx = cdiv(cols, 256);
   if (gx > 32) gx = 32;
@@ -345,6 +361,11 @@ void merge_lane_stats(pluq_ctx* c, const pluq_ctx* l) {
   c->n_gemm += l->n_gemm;
 }
 
+// Whether a recursive call's local row / column index vectors are the identity.
+struct Ident {
+  bool r = true, c = true;
+};
+
 struct Recursion {
   pluq_ctx* c;
   uint32_t* A;
@@ -362,7 +383,7 @@ struct Recursion {
   // Runs the recursive calls on F and G at once on the two child contexts
   // (this thread takes G); returns after both streams have finished.
   int fork_fg(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2, int64_t r1,
-              int d, int64_t* r2, int64_t* r3) {
+              int d, int64_t* r2, int64_t* r3, Ident* id2, Ident* id3) {
     pluq_ctx* lf = nullptr;
     pluq_ctx* lg = nullptr;
     // F's lane also runs f_post: D and H (r1 + m2 rows) by F's columns
@@ -390,12 +411,12 @@ struct Recursion {
         return;
       }
       Recursion rf{lf, A, lda, lf->small.as<int32_t>() + 8};
-      int st = rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2);
-      if (st == PLUQ_OK) st = rf.f_post(R0, C0, m1, n1, m2, n2, r1, *r2, d);
+      int st = rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2, id2);
+      if (st == PLUQ_OK) st = rf.f_post(R0, C0, m1, n1, m2, n2, r1, *r2, d, *id2);
       st_f = finish(lf, st);
     });
     Recursion rg{lg, A, lda, lg->small.as<int32_t>() + 8};
-    st_g = finish(lg, rg.node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, r3));
+    st_g = finish(lg, rg.node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, r3, id3));
     tf.join();
     merge_lane_stats(c, lf);
     merge_lane_stats(c, lg);
@@ -409,15 +430,16 @@ struct Recursion {
   // row by row, so they commute with G's later row permutation of H and run
   // in F's branch while G is still being factored.
   int f_post(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2, int64_t r1,
-             int64_t r2, int d) {
+             int64_t r2, int d, Ident id2) {
     int32_t* pr = PR(d) + R0;
     int32_t* pc = PC(d) + C0;
     int32_t* cr = PR(d + 1);
     int32_t* cc = PC(d + 1);
-    PLUQ_TRY(launch_compose_pair(c, pr + r1, cr + R0 + r1, m1 - r1, pc + n1, cc + C0 + n1, n2));
-    PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
+    PLUQ_TRY(compose_pair(pr + r1, cr + R0 + r1, m1 - r1, pc + n1, cc + C0 + n1, n2, id2));
+    if (!id2.r) PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
     // D (rows 0..r1) and H (rows m1..m) by F's column permutation
-    PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
+    if (!id2.c)
+      PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
     if (r2 > 0) {
       PLUQ_TRY(trsm_right_upper(c, X(R0, C0, r1, n1), lda, r2, X(R0, C0, m1, n1), lda, m2));
       PLUQ_TRY(fgemm_sub(c, m2, n2 - r2, r2, X(R0, C0, m1, n1), lda, X(R0, C0, r1, n1 + r2), lda,
@@ -458,10 +480,24 @@ struct Recursion {
     return PLUQ_OK;
   }
 
-  int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out) {
+  // Composition with a child's local index vectors; a child whose vectors are
+  // the identity changes nothing, so its launch is skipped.
+  int compose_pair(int32_t* base_r, const int32_t* perm_r, int64_t count_r, int32_t* base_c,
+                   const int32_t* perm_c, int64_t count_c, Ident id) {
+    if (id.r && id.c) return PLUQ_OK;
+    if (id.r) return launch_compose(c, base_c, perm_c, count_c);
+    if (id.c) return launch_compose(c, base_r, perm_r, count_r);
+    return launch_compose_pair(c, base_r, perm_r, count_r, base_c, perm_c, count_c);
+  }
+
+  // Factors the m x n block at (R0, C0); *r_out receives its rank and *id
+  // whether its local row / column index vectors are the identity (then the
+  // caller's permutations of the blocks beside it are no-ops and skipped).
+  int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out, Ident* id) {
     int32_t* pr = PR(d) + R0;
     int32_t* pc = PC(d) + C0;
     *r_out = 0;
+    *id = Ident{};
     if (m == 0 || n == 0) {
       PLUQ_TRY(launch_iota_pair(c, pr, m, pc, n));
       return PLUQ_OK;
@@ -485,12 +521,21 @@ struct Recursion {
         PLUQ_TRY(launch_leaf_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
       else
         PLUQ_TRY(launch_base_pluq(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      // whether the leaf's index vectors are the identity (ints 12, 13)
+      {
+        ProfScope ps(c, PC_INDEX, 0, 4.0 * (m + n));
+        k_perm_identity<<<1, 1024, 0, c->stream>>>(pr, (int)m, pc, (int)n,
+                                                    c->small.as<int32_t>() + 12);
+        PLUQ_CUDA(cudaGetLastError());
+      }
       // rank (int 8 of the scalar block) and the device error word (int 16)
       PLUQ_CUDA(cudaMemcpyAsync(c->host_small, c->small.ptr, 32 * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, c->stream));
       PLUQ_CUDA(cudaStreamSynchronize(c->stream));
       if (c->host_small[16] != 0) return c->host_small[16];
       *r_out = c->host_small[8];
+      id->r = c->host_small[12] != 0;
+      id->c = c->host_small[13] != 0;
       if (chain || cluster || leaf) c->leaf_density = (double)*r_out / (double)std::min(m, n);
       return PLUQ_OK;
     }
@@ -530,10 +575,11 @@ struct Recursion {
 
     // A1
     int64_t r1 = 0;
-    PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1));
-    PLUQ_TRY(launch_compose_pair(c, pr, cr + R0, m1, pc, cc + C0, n1));
-    PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
-    PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
+    Ident id1, id2, id3, id4;
+    PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1, &id1));
+    PLUQ_TRY(compose_pair(pr, cr + R0, m1, pc, cc + C0, n1, id1));
+    if (!id1.r) PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
+    if (!id1.c) PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
     if (r1 > 0) {
       // D = L1^{-1} B1 and E = C1 U1^{-1} are independent, and so is G's
       // update (it needs E only): E and G -= E V1 go to the G child context's
@@ -562,16 +608,17 @@ struct Recursion {
                       (m1 - r1) * n2 >= fork_min && m2 * (n1 - r1) >= fork_min;
     if (fork) {
       // F's branch also runs f_post (see there)
-      PLUQ_TRY(fork_fg(R0, C0, m1, n1, m2, n2, r1, d, &r2, &r3));
+      PLUQ_TRY(fork_fg(R0, C0, m1, n1, m2, n2, r1, d, &r2, &r3, &id2, &id3));
     } else {
-      PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2));
-      PLUQ_TRY(f_post(R0, C0, m1, n1, m2, n2, r1, r2, d));
-      PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3));
+      PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2, &id2));
+      PLUQ_TRY(f_post(R0, C0, m1, n1, m2, n2, r1, r2, d, id2));
+      PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3, &id3));
     }
-    PLUQ_TRY(launch_compose_pair(c, pr + m1, cr + R0 + m1, m2, pc + r1, cc + C0 + r1, n1 - r1));
+    PLUQ_TRY(compose_pair(pr + m1, cr + R0 + m1, m2, pc + r1, cc + C0 + r1, n1 - r1, id3));
     // E (columns 0..r1) and H (columns n1..n) by G's row permutation
-    PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
-    PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
+    if (!id3.r)
+      PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
+    if (!id3.c) PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
 
     // H = [H1 H2; H3 H4] at rows m1.., columns n1.. ([I; K] and H2 are done
     // in f_post): O = L3^{-1} H[:r3, r2:], R -= M3 O
@@ -584,21 +631,26 @@ struct Recursion {
 
     // R
     int64_t r4 = 0;
-    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4));
-    PLUQ_TRY(launch_compose_pair(c, pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3, pc + n1 + r2,
-                                 cc + C0 + n1 + r2, n2 - r2));
+    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4, &id4));
+    PLUQ_TRY(compose_pair(pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3, pc + n1 + r2,
+                          cc + C0 + n1 + r2, n2 - r2, id4));
     // E2, M3 (columns 0..r1+r3) and K (columns n1..n1+r2) by R's row permutation
-    PLUQ_TRY(permute_rows2(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, 0, r1 + r3, n1, r2,
-                           cr + R0 + m1 + r3));
+    if (!id4.r)
+      PLUQ_TRY(permute_rows2(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, 0, r1 + r3, n1, r2,
+                             cr + R0 + m1 + r3));
     // D2, V2 (rows 0..r1+r2) and O (rows m1..m1+r3) by R's column permutation
-    PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1 + r2), lda, 0, r1 + r2, m1, r3, n2 - r2,
-                           cc + C0 + n1 + r2));
+    if (!id4.c)
+      PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1 + r2), lda, 0, r1 + r2, m1, r3, n2 - r2,
+                             cc + C0 + n1 + r2));
+    id->r = id1.r && id2.r && id3.r && id4.r;
+    id->c = id1.c && id2.c && id3.c && id4.c;
 
     // block-cyclic shifts
     int32_t* tmp = PR(spare()) + R0;  // spare row slot (this block's range)
     {
       const int64_t a = r1 + r2, fr = m1 - r1 - r2, gr = r3 + r4;
       if (fr > 0 && gr > 0) {
+        id->r = false;
         const int64_t st[2] = {fr, 0}, ln[2] = {gr, fr};
         PLUQ_TRY(launch_segperm(c, tmp, st, ln, 2));
         PLUQ_TRY(permute_rows(c, X(R0, C0, a, 0), lda, fr + gr, n, tmp));
@@ -610,6 +662,7 @@ struct Recursion {
       const int64_t gn = n1 - r1 - r3;
       const bool ident = (r2 == 0 || (r3 == 0 && gn == 0)) && (r4 == 0 || gn == 0);
       if (!ident) {
+        id->c = false;
         int32_t* tmpc = PC(spare()) + C0;
         const int64_t st[4] = {r3 + gn, 0, r3 + gn + r2, r3};
         const int64_t ln[4] = {r2, r3, r4, gn};
@@ -701,7 +754,8 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
     if (c->host_small[0] != 0) return PLUQ_ERR_ENTRY_OUT_OF_RANGE;
   }
   Recursion rec{c, A, lda, c->small.as<int32_t>() + 8};
-  PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out));
+  Ident id;
+  PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out, &id));
   PLUQ_CUDA(cudaMemcpyAsync(c->host_small, c->small.ptr, 32 * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, c->stream));
   PLUQ_CUDA(cudaStreamSynchronize(c->stream));

@@ -403,94 +403,131 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   }
 }
 
+// Signed base-2^8 digits of a balanced residue x, |x| <= p/2: the low L - 1
+// digits in [-2^7, 2^7), the top digit whatever remains, each exact in FP16.
+template <int L>
+__device__ __forceinline__ void split_digits(int32_t x, __half (&d)[L]) {
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    int32_t v;
+    if (l == L - 1) {
+      v = x;
+    } else {
+      v = ((x + (1 << (kLimbBits - 1))) & ((1 << kLimbBits) - 1)) - (1 << (kLimbBits - 1));
+      x = (x - v) >> kLimbBits;
+    }
+    d[l] = __int2half_rn(v);
+  }
+}
+
+__device__ __forceinline__ int32_t balance(uint32_t a, uint32_t p) {
+  return a > (p - 1) / 2 ? (int32_t)(a - p) : (int32_t)a;
+}
+
 // Digit planes of A (M x K) in K-major layout: out[l][i][k], rows padded to
-// Mp and columns to Kp with zeros.
+// Mp and columns to Kp (a multiple of 64) with zeros.  A thread takes 8
+// consecutive k of one row and writes 16 bytes per plane; `vec` marks a
+// 16-byte aligned A (base and row stride), read as two 16-byte loads.
 template <int L>
 __device__ __forceinline__ void pack_rows(const uint32_t* __restrict__ A, int64_t lda, int64_t M,
-                                          int64_t K, int64_t Mp, int64_t Kp, uint32_t p,
-                                          __half* __restrict__ out, int bx, int by, int gx,
-                                          int gy, int tid, int nthreads) {
-  const int64_t half_p = (p - 1) / 2;
-  for (int64_t i = by; i < Mp; i += gy)
-  for (int64_t k = (int64_t)bx * nthreads + tid; k < Kp; k += (int64_t)gx * nthreads) {
-    int32_t x = 0;
-    if (i < M && k < K) {
-      const int64_t a = A[i * lda + k];
-      x = (int32_t)(a > half_p ? a - (int64_t)p : a);
+                                          int64_t K, int64_t Mp, int64_t Kp, uint32_t p, bool vec,
+                                          __half* __restrict__ out, int64_t item0,
+                                          int64_t nitems_step) {
+  const int64_t chunks = Kp / 8, total = Mp * chunks;
+  for (int64_t it = item0; it < total; it += nitems_step) {
+    const int64_t i = it / chunks, k0 = (it - i * chunks) * 8;
+    uint32_t a[8];
+    if (i < M && vec && k0 + 8 <= K) {
+      const uint4* src = reinterpret_cast<const uint4*>(A + i * lda + k0);
+      const uint4 u0 = __ldg(src), u1 = __ldg(src + 1);
+      a[0] = u0.x; a[1] = u0.y; a[2] = u0.z; a[3] = u0.w;
+      a[4] = u1.x; a[5] = u1.y; a[6] = u1.z; a[7] = u1.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = (i < M && k0 + q < K) ? __ldg(A + i * lda + k0 + q) : 0u;
+    }
+    __align__(16) __half h[L][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      __half d[L];
+      split_digits<L>(balance(a[q], p), d);
+#pragma unroll
+      for (int l = 0; l < L; ++l) h[l][q] = d[l];
     }
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-      int32_t d;
-      if (l == L - 1) {
-        d = x;
-      } else {
-        d = ((x + (1 << (kLimbBits - 1))) & ((1 << kLimbBits) - 1)) - (1 << (kLimbBits - 1));
-        x = (x - d) >> kLimbBits;
-      }
-      out[(int64_t)l * Mp * Kp + i * Kp + k] = __int2half_rn(d);
-    }
+    for (int l = 0; l < L; ++l)
+      *reinterpret_cast<uint4*>(out + (int64_t)l * Mp * Kp + i * Kp + k0) =
+          *reinterpret_cast<const uint4*>(h[l]);
   }
 }
 
 // Digit planes of B^T: B is K x N row-major; out[l][j][k] (K-major rows of
-// B^T), padded to Np x Kp.  32 x 32 tiles transposed through shared memory.
+// B^T), padded to Np x Kp.  A 64 (k) x 64 (j) tile is staged in shared memory
+// as balanced residues (16-byte loads along j when B is aligned), then each
+// thread writes 8 consecutive k of one j: 16 bytes per plane.
+constexpr int kPackT = 64;
+
 template <int L>
 __device__ __forceinline__ void pack_cols(const uint32_t* __restrict__ B, int64_t ldb, int64_t K,
-                                          int64_t N, int64_t Np, int64_t Kp, uint32_t p,
-                                          __half* __restrict__ out, int bx, int by, int tx,
-                                          int ty) {
-  __shared__ int32_t tile[32][33];
-  const int64_t k0 = (int64_t)bx * 32, j0 = (int64_t)by * 32;  // 32 x 8 threads
-  const int64_t half_p = (p - 1) / 2;
-  for (int yy = ty; yy < 32; yy += 8) {
-    const int64_t k = k0 + yy, j = j0 + tx;
-    int32_t x = 0;
-    if (k < K && j < N) {
-      const int64_t b = B[k * ldb + j];
-      x = (int32_t)(b > half_p ? b - (int64_t)p : b);
+                                          int64_t N, int64_t Np, int64_t Kp, uint32_t p, bool vec,
+                                          __half* __restrict__ out, int tk, int tj, int tid) {
+  __shared__ int32_t tile[kPackT][kPackT + 1];
+  const int64_t k0 = (int64_t)tk * kPackT, j0 = (int64_t)tj * kPackT;
+  // load: 64 rows x 16 four-element groups; 256 threads, 4 groups each
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int g = tid + q * 256, kk = g >> 4, jj = (g & 15) * 4;
+    const int64_t k = k0 + kk, j = j0 + jj;
+    uint32_t v[4];
+    if (k < K && vec && j + 4 <= N) {
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(B + k * ldb + j));
+      v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (k < K && j + e < N) ? __ldg(B + k * ldb + j + e) : 0u;
     }
-    tile[yy][tx] = x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tile[kk][jj + e] = balance(v[e], p);
   }
   __syncthreads();
-  for (int yy = ty; yy < 32; yy += 8) {
-    const int64_t j = j0 + yy, k = k0 + tx;
-    if (j >= Np || k >= Kp) continue;
-    int32_t x = tile[tx][yy];
+  // store: 64 j x 8 chunks of 8 k; eight consecutive threads write the 128
+  // contiguous bytes of one j (per plane)
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-      int32_t d;
-      if (l == L - 1) {
-        d = x;
-      } else {
-        d = ((x + (1 << (kLimbBits - 1))) & ((1 << kLimbBits) - 1)) - (1 << (kLimbBits - 1));
-        x = (x - d) >> kLimbBits;
-      }
-      out[(int64_t)l * Np * Kp + j * Kp + k] = __int2half_rn(d);
+  for (int half = 0; half < 2; ++half) {
+    const int item = tid + 256 * half, jj = item >> 3, kc = (item & 7) * 8;
+    const int64_t j = j0 + jj, k = k0 + kc;
+    if (j >= Np || k >= Kp) continue;
+    __align__(16) __half h[L][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      __half d[L];
+      split_digits<L>(tile[kc + q][jj], d);
+#pragma unroll
+      for (int l = 0; l < L; ++l) h[l][q] = d[l];
     }
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+      *reinterpret_cast<uint4*>(out + (int64_t)l * Np * Kp + j * Kp + k) =
+          *reinterpret_cast<const uint4*>(h[l]);
   }
 }
 
-// Both operands' digit planes in one launch: z = 0 packs A (grid ga), z = 1
-// packs B^T (grid gb, 32 x 8 threads as 256); blocks outside a part's grid
-// return at once.
-struct PackGrid {
-  int x, y;
-};
-
+// Both operands' digit planes in one launch: blocks [0, ga) pack A
+// (grid-stride over 8-element items), blocks [ga, ga + gbk * gbj) pack one
+// 64 x 64 tile of B^T each.
 template <int L>
 __global__ void __launch_bounds__(256)
     k_pack_both(const uint32_t* __restrict__ A, int64_t lda, int64_t M, int64_t Mp,
                 const uint32_t* __restrict__ B, int64_t ldb, int64_t N, int64_t Np, int64_t K,
                 int64_t Kp, uint32_t p, __half* __restrict__ outA, __half* __restrict__ outB,
-                PackGrid ga, PackGrid gb) {
-  if (blockIdx.z == 0) {
-    if ((int)blockIdx.x >= ga.x || (int)blockIdx.y >= ga.y) return;
-    pack_rows<L>(A, lda, M, K, Mp, Kp, p, outA, blockIdx.x, blockIdx.y, ga.x, ga.y, threadIdx.x,
-                 256);
+                int ga, int gbk, bool veca, bool vecb) {
+  const int b = blockIdx.x;
+  if (b < ga) {
+    pack_rows<L>(A, lda, M, K, Mp, Kp, p, veca, outA, (int64_t)b * 256 + threadIdx.x,
+                 (int64_t)ga * 256);
   } else {
-    if ((int)blockIdx.x >= gb.x || (int)blockIdx.y >= gb.y) return;
-    pack_cols<L>(B, ldb, K, N, Np, Kp, p, outB, blockIdx.x, blockIdx.y, threadIdx.x & 31,
-                 threadIdx.x >> 5);
+    const int t = b - ga;
+    pack_cols<L>(B, ldb, K, N, Np, Kp, p, vecb, outB, t % gbk, t / gbk, threadIdx.x);
   }
 }
 
@@ -498,10 +535,15 @@ template <int L>
 int launch_pack(cudaStream_t s, const uint32_t* A, int64_t lda, int64_t M, int64_t Mp,
                 const uint32_t* B, int64_t ldb, int64_t N, int64_t Np, int64_t K, int64_t Kp,
                 uint32_t p, __half* Ap, __half* Bp) {
-  const PackGrid ga{(int)std::min<int64_t>(cdiv(Kp, 256), 64), (int)std::min<int64_t>(Mp, 65535)};
-  const PackGrid gb{(int)cdiv(Kp, 32), (int)cdiv(Np, 32)};
-  const dim3 g((unsigned)std::max(ga.x, gb.x), (unsigned)std::max(ga.y, gb.y), 2);
-  k_pack_both<L><<<g, 256, 0, s>>>(A, lda, M, Mp, B, ldb, N, Np, K, Kp, p, Ap, Bp, ga, gb);
+  // A: about 16 items (8 elements each) per thread, at most 8 CTAs per SM-ish
+  const int64_t itemsA = Mp * (Kp / 8);
+  const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(itemsA, 256 * 16), 4096));
+  const int64_t gbk = cdiv(Kp, kPackT), gbj = cdiv(Np, kPackT);
+  if (ga + gbk * gbj > INT32_MAX) return PLUQ_ERR_INVALID_ARG;
+  const bool veca = ((reinterpret_cast<uintptr_t>(A) | (uintptr_t)(lda * 4)) & 15u) == 0;
+  const bool vecb = ((reinterpret_cast<uintptr_t>(B) | (uintptr_t)(ldb * 4)) & 15u) == 0;
+  k_pack_both<L><<<(unsigned)(ga + gbk * gbj), 256, 0, s>>>(A, lda, M, Mp, B, ldb, N, Np, K, Kp,
+                                                            p, Ap, Bp, ga, (int)gbk, veca, vecb);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
@@ -636,14 +678,13 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   __half* Bp = reinterpret_cast<__half*>(reinterpret_cast<char*>(Ap) + ((abytes + 1023) / 1024) * 1024);
   {
     ProfScope ps(c, PC_PACK, 0, 4.0 * (M * K + K * N) + (double)abytes + (double)bbytes, 1);
-    if (cdiv(Np, 32) > 65535) return PLUQ_ERR_INVALID_ARG;
     PLUQ_TRY(launch_pack<L>(c->stream, A, lda, M, Mp, B, ldb, N, Np, K, Kp, c->F.p, Ap, Bp));
   }
   CUtensorMap ma, mb;
   PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp, kTM));
   PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp, TN));
   const dim3 grid((unsigned)(Np / TN), (unsigned)(Mp / kTM));
-  if (grid.y > 65535 || cdiv(Np, 32) > 65535) return PLUQ_ERR_INVALID_ARG;
+  if (grid.y > 65535) return PLUQ_ERR_INVALID_ARG;
   int* err = c->small.as<int>() + 16;
   ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K,
                (double)abytes + (double)bbytes + 8.0 * M * N, 1,
@@ -762,7 +803,7 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
   const size_t abytes = sizeof(__half) * L * Mp * Kp, bbytes = sizeof(__half) * L * Np * Kp;
   const size_t aoff = ((abytes + 1023) / 1024) * 1024;
   if (aoff + bbytes > kNoAllocScratchBytes) return PLUQ_ERR_TOO_LARGE;
-  if (cdiv(Np, 32) > 65535 || Mp / kTM > 65535) return PLUQ_ERR_TOO_LARGE;
+  if (Mp / kTM > 65535) return PLUQ_ERR_TOO_LARGE;
   __half* Ap = reinterpret_cast<__half*>(d.scratch);
   __half* Bp = reinterpret_cast<__half*>(d.scratch + aoff);
   PLUQ_CUDA(cudaMemsetAsync(d.err, 0, sizeof(int), s));

@@ -474,48 +474,6 @@ def test_status_codes(ctx):
     assert_parity(ctx, workloads.uniform_matrix(50, 50, 131071, 1), 131071)
 
 
-# ------------------------------------------------ workload-size parity --
-
-def test_config_uniform_1024(ctx):
-    cfg = workloads.CONFIGS["uniform-1024-p131071"]
-    for seed in (1, 2):
-        A = workloads.uniform_matrix(cfg.m, cfg.n, cfg.p, seed)
-        assert_parity(ctx, A, cfg.p, "limb")
-        assert_parity(ctx, A, cfg.p, "fp64")
-
-
-def freivalds(A, p, P, Q, LU, r, trials=2, seed=0):
-    """Random-vector check of A[P][:, Q] = L U mod p (error < p^-trials)."""
-    rng = np.random.default_rng(seed)
-    m, n = A.shape
-    A64 = A.astype(np.int64)
-    L = LU[:, :r].astype(np.int64)
-    U = LU[:r, :].astype(np.int64)
-    for _ in range(trials):
-        x = rng.integers(0, p, n, dtype=np.int64)
-        z = np.zeros(n, dtype=np.int64)
-        z[Q] = x  # (A Q^T x)  = A z
-        lhs = (A64 @ z % p)[P] if p < 2 ** 20 else matmul_mod(A64, z[:, None], p)[:, 0][P]
-        ux = np.triu(U) @ x % p if p < 2 ** 20 else matmul_mod(np.triu(U), x[:, None], p)[:, 0]
-        Lt = np.tril(L, -1)
-        Lt[np.arange(r), np.arange(r)] = 1
-        rhs = (Lt @ ux) % p if p < 2 ** 20 else matmul_mod(Lt, ux[:, None], p)[:, 0]
-        assert np.array_equal(lhs % p, rhs), "Freivalds check of P L U Q = A failed"
-
-
-@pytest.mark.parametrize("form", ["limb", "fp64"])
-def test_config_lru_8192(ctx, form):
-    cfg = workloads.CONFIGS["lru-8192-r4096-p131071"]
-    g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
-    r, P, Q, LU, rrp, crp = run_pluq(ctx, g.A, cfg.p, form)
-    assert r == cfg.r
-    check_rpm_from_pq(P, Q, r, g.rpm)
-    assert rrp.tolist() == g.rrp.tolist() and crp.tolist() == g.crp.tolist()
-    assert not np.any(LU[r:, r:])
-    assert np.all(np.diag(LU[:r, :r]) != 0)
-    freivalds(g.A, cfg.p, P, Q, LU, r)
-
-
 # ------------------------------------------------------------- batched --
 
 def _batch_cases(p, seed):
@@ -599,103 +557,6 @@ def test_batched_bad_entry_status(ctx):
     torch.cuda.synchronize()
     assert status == [0, -4, 0] and ranks[0] == ranks[2] == 20
     assert torch.equal(As[1], keep)
-
-
-def freivalds_f64(A, p, P, Q, LU, r, trials=2, seed=0):
-    """Exact float64 Freivalds check of A[P][:, Q] = L U mod p for p < 2^16.
-
-    Entries and vector entries below 2^16 keep every product below 2^32 and
-    every row sum of up to 2^21 terms below 2^53, so float64 sums are exact.
-    """
-    assert p < 2 ** 16
-    rng = np.random.default_rng(seed)
-    m, n = A.shape
-    step = 2048
-    for _ in range(trials):
-        x = rng.integers(0, p, n).astype(np.float64)
-        z = np.zeros(n)
-        z[Q] = x
-        lhs = np.concatenate([np.mod(A[i:i + step].astype(np.float64) @ z, p)
-                              for i in range(0, m, step)])[P]
-        # U x: U[t, u] for u >= t, t < r (rows of the compressed storage)
-        ux = np.concatenate([np.mod(np.triu(LU[i:min(r, i + step), :].astype(np.float64), i) @ x, p)
-                             for i in range(0, r, step)]) if r else np.zeros(0)
-        rhs = np.zeros(m)
-        for i in range(0, m, step):
-            rows = np.arange(i, min(m, i + step))
-            Lb = np.where(np.arange(r)[None, :] < rows[:, None],
-                          LU[i:i + step, :r].astype(np.float64), 0.0)
-            on_diag = rows < r
-            Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1.0
-            rhs[i:i + step] = np.mod(Lb @ ux, p)
-        assert np.array_equal(lhs, rhs), "Freivalds check of P L U Q = A failed"
-
-
-@pytest.mark.parametrize("form", ["limb"])
-def test_config_uniform_32768(ctx, form):
-    """Full-size 32768^2 over GF(65521): RPM on blocks the oracle can factor, Freivalds."""
-    cfg = workloads.CONFIGS["uniform-32768-p65521"]
-    m, n, p = cfg.m, cfg.n, cfg.p
-    A = workloads.uniform_matrix(m, n, p, seed=1)
-    res = pq.pluq_modp(to_dev(A), p, form=form, ctx=ctx)
-    torch.cuda.synchronize()
-    r = res.rank
-    P = res.P.cpu().numpy()
-    Q = res.Q.cpu().numpy()
-    LU = res.LU.cpu().numpy()
-    assert sorted(P.tolist()) == list(range(m)) and sorted(Q.tolist()) == list(range(n))
-    rpm = set(zip(P[:r].tolist(), Q[:r].tolist()))
-    # the rank profile matrix of a leading block is the restriction of A's
-    for (i, j) in [(1536, 1536), (192, n), (m, 160)]:
-        ref = oracle.pluq(np.ascontiguousarray(A[:i, :j]), p, want_lu=False)
-        assert {(a, b) for (a, b) in rpm if a < i and b < j} == ref.rpm, (i, j)
-    assert not np.any(LU[r:, r:])
-    assert np.all(np.diag(LU[:r, :r]) != 0)
-    freivalds_f64(A, p, P, Q, LU, r)
-
-
-def freivalds_blocked(A, p, P, Q, LU, r, trials=1, seed=0, step=1024):
-    """Freivalds check of A[P][:, Q] = L U mod p by row blocks, exact int64 for any p < 2^31."""
-    rng = np.random.default_rng(seed)
-    m, n = A.shape
-
-    def mv(X, v):
-        return matmul_mod(X, v[:, None], p)[:, 0]
-
-    for _ in range(trials):
-        x = rng.integers(0, p, n, dtype=np.int64)
-        z = np.zeros(n, dtype=np.int64)
-        z[Q] = x
-        lhs = np.concatenate([mv(A[i:i + step], z) for i in range(0, m, step)])[P]
-        ux = (np.concatenate([mv(np.triu(LU[i:min(r, i + step)].astype(np.int64), i), x)
-                              for i in range(0, r, step)]) if r else np.zeros(0, np.int64))
-        rhs = np.zeros(m, dtype=np.int64)
-        for i in range(0, m, step):
-            rows = np.arange(i, min(m, i + step))
-            Lb = np.where(np.arange(r)[None, :] < rows[:, None], LU[i:i + step, :r].astype(np.int64), 0)
-            on_diag = rows < r
-            Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1
-            rhs[i:i + step] = mv(Lb, ux)
-        assert np.array_equal(lhs, rhs), "Freivalds check of P L U Q = A failed"
-
-
-@pytest.mark.parametrize("form", ["limb"])
-def test_config_lru_16384x20480_p31(ctx, form):
-    """Full-size 16384 x 20480, rank 16320, over GF(2^31 - 1): RPM by construction, Freivalds."""
-    cfg = workloads.CONFIGS["lru-16384x20480-r16320-p2147483647"]
-    g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
-    res = pq.pluq_modp(to_dev(g.A), cfg.p, form=form, ctx=ctx)
-    torch.cuda.synchronize()
-    r = res.rank
-    P, Q = res.P.cpu().numpy(), res.Q.cpu().numpy()
-    assert r == cfg.r
-    check_rpm_from_pq(P, Q, r, g.rpm)
-    assert res.rrp.cpu().numpy().tolist() == g.rrp.tolist()
-    assert res.crp.cpu().numpy().tolist() == g.crp.tolist()
-    LU = res.LU.cpu().numpy().view(np.uint32)
-    assert not np.any(LU[r:, r:])
-    assert np.all(np.diag(LU[:r, :r]) != 0)
-    freivalds_blocked(g.A, cfg.p, P, Q, LU, r)
 
 
 # ------------------------------------------------------------- autotuner --
