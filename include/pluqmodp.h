@@ -283,6 +283,18 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *   PLUQ_OPT_USE_TUNED   1 (default): factorizations whose (p, m, n, form)
  *                        was autotuned use the tuned schedule in place of
  *                        LEAF_DIM, LEAF_KIND and FORK_DEPTH; 0: ignore it.
+ *   PLUQ_OPT_WAIT_LIMIT_US  bound of every spin-wait of the cooperative leaf
+ *                        kernels (kinds 0 and 1) on a memory word, in
+ *                        microseconds at a 2 GHz SM clock [0, 6e7] (default
+ *                        2e6): a wait that runs out records PLUQ_ERR_TIMEOUT,
+ *                        every CTA of the launch returns, the call returns
+ *                        that status and the context stays usable.  0 makes
+ *                        any wait that is not satisfied at once run out.
+ *   PLUQ_OPT_WORKSPACE_MB  cap on the device workspace the context (with its
+ *                        child contexts) holds, in MiB [0, 2^31); 0 (default):
+ *                        none.  A call whose workspace would exceed the cap
+ *                        returns PLUQ_ERR_NO_WORKSPACE; buffers already held
+ *                        stay allocated until the context is destroyed.
  * Errors: INVALID_ARG for an unknown option or a value out of range. */
 #define PLUQ_OPT_LEAF_DIM 1
 #define PLUQ_OPT_LEAF_KIND 2
@@ -295,6 +307,8 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_THIN_GEMM 9
 #define PLUQ_OPT_DECOMPOSITION 10
 #define PLUQ_OPT_SLAB_ROWS 11
+#define PLUQ_OPT_WAIT_LIMIT_US 12
+#define PLUQ_OPT_WORKSPACE_MB 13
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "pluqmodp.h"
@@ -66,25 +67,39 @@ __device__ __forceinline__ void copy_rows_g2s(uint32_t* __restrict__ dst,
   }
 }
 
+// Device workspace held by a context and its child contexts, against an
+// optional cap (0: none).
+struct WsAccount {
+  std::atomic<size_t> used{0};  // child contexts grow buffers from their own threads
+  size_t limit = 0;
+};
+
 // A growable device allocation owned by the context.
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  WsAccount* acct = nullptr;  // the context's workspace account (may be null)
   int ensure(size_t need) {
     if (need <= bytes) return PLUQ_OK;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    bytes = 0;
     size_t want = need + need / 8 + 256;
+    if (acct && acct->limit && acct->used - bytes + want > acct->limit) {
+      // try the exact size before giving up
+      want = need;
+      if (acct->used - bytes + want > acct->limit) return PLUQ_ERR_NO_WORKSPACE;
+    }
+    release();
     if (cudaMalloc(&ptr, want) != cudaSuccess) {
       cudaGetLastError();
+      ptr = nullptr;
       return PLUQ_ERR_NO_WORKSPACE;
     }
     bytes = want;
+    if (acct) acct->used += want;
     return PLUQ_OK;
   }
   void release() {
     if (ptr) cudaFree(ptr);
+    if (acct && ptr) acct->used -= bytes;
     ptr = nullptr;
     bytes = 0;
   }
@@ -124,6 +139,9 @@ struct Profiler {
 
 struct pluq_ctx {
   Profiler prof;
+  WsAccount ws_own;            // the user's context: its account
+  WsAccount* ws = &ws_own;     // child contexts: the parent's account
+  long long wait_cycles = 4000000000LL;  // bound of device waits (~2 s at 2 GHz)
   int64_t launches[PC_COUNT] = {0, 0, 0, 0, 0, 0, 0};
   int device = 0;
   int sm_count = 0;
@@ -197,6 +215,14 @@ struct pluq_ctx {
   int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
   // device error flag (int) lives in small at offset 0
 };
+
+// Points every workspace buffer of c at the account c->ws.
+inline void bind_workspace(pluq_ctx* c) {
+  for (DevBuf* b : {&c->scratch, &c->pack, &c->perm_r, &c->perm_c, &c->tmp_i, &c->tri_inv,
+                    &c->small, &c->inv_table, &c->work, &c->leaf, &c->batch_dev,
+                    &c->batch_scratch, &c->batch_pq, &c->tune_src, &c->tune_dst})
+    b->acct = c->ws;
+}
 
 // Count a kernel launch of class `cls` and, when profiling, bracket it with a
 // pair of CUDA events on the context stream (work = algorithmic flops/bytes).

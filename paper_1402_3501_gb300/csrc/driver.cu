@@ -299,6 +299,8 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
     pluq_ctx* nl = new pluq_ctx();
     nl->device = c->device;
     nl->parent = c;
+    nl->ws = c->ws;
+    bind_workspace(nl);
     nl->lane_depth = c->lane_depth + 1;
     if (cudaStreamCreateWithFlags(&nl->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&nl->host_small, 256) != cudaSuccess) {
@@ -310,6 +312,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   }
   l->stream = l->own_stream;
   l->sm_count = std::max(1, c->sm_count / 2);
+  l->wait_cycles = c->wait_cycles;
   l->F = c->F;
   l->form = c->form;
   l->bm = c->bm;
@@ -366,6 +369,14 @@ struct Ident {
   bool r = true, c = true;
 };
 
+// Which parts of a block's factorization must end in their compressed
+// positions: L (unit lower, with M), U (upper, with V), both, or neither (only
+// the index vectors and the rank).  A full PLUQ keeps both everywhere.  The
+// reduced echelon form needs U only and the rank profiles neither, at the top;
+// a child keeps what its parent still reads after it returns (all of A1; U2,
+// V2 of F; L3, M3 of G) plus the parent's own needs for its block.
+enum Keep { KEEP_NONE = 0, KEEP_L = 1, KEEP_U = 2, KEEP_LU = 3 };
+
 struct Recursion {
   pluq_ctx* c;
   uint32_t* A;
@@ -383,7 +394,7 @@ struct Recursion {
   // Runs the recursive calls on F and G at once on the two child contexts
   // (this thread takes G); returns after both streams have finished.
   int fork_fg(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2, int64_t r1,
-              int d, int64_t* r2, int64_t* r3, Ident* id2, Ident* id3) {
+              int d, int64_t* r2, int64_t* r3, Ident* id2, Ident* id3, int keep) {
     pluq_ctx* lf = nullptr;
     pluq_ctx* lg = nullptr;
     // F's lane also runs f_post: D and H (r1 + m2 rows) by F's columns
@@ -411,12 +422,12 @@ struct Recursion {
         return;
       }
       Recursion rf{lf, A, lda, lf->small.as<int32_t>() + 8};
-      int st = rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2, id2);
-      if (st == PLUQ_OK) st = rf.f_post(R0, C0, m1, n1, m2, n2, r1, *r2, d, *id2);
+      int st = rf.node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, r2, id2, keep | KEEP_U);
+      if (st == PLUQ_OK) st = rf.f_post(R0, C0, m1, n1, m2, n2, r1, *r2, d, *id2, keep);
       st_f = finish(lf, st);
     });
     Recursion rg{lg, A, lda, lg->small.as<int32_t>() + 8};
-    st_g = finish(lg, rg.node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, r3, id3));
+    st_g = finish(lg, rg.node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, r3, id3, keep | KEEP_L));
     tf.join();
     merge_lane_stats(c, lf);
     merge_lane_stats(c, lg);
@@ -430,16 +441,22 @@ struct Recursion {
   // row by row, so they commute with G's later row permutation of H and run
   // in F's branch while G is still being factored.
   int f_post(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2, int64_t r1,
-             int64_t r2, int d, Ident id2) {
+             int64_t r2, int d, Ident id2, int keep) {
     int32_t* pr = PR(d) + R0;
     int32_t* pc = PC(d) + C0;
     int32_t* cr = PR(d + 1);
     int32_t* cc = PC(d + 1);
     PLUQ_TRY(compose_pair(pr + r1, cr + R0 + r1, m1 - r1, pc + n1, cc + C0 + n1, n2, id2));
-    if (!id2.r) PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));  // M1
-    // D (rows 0..r1) and H (rows m1..m) by F's column permutation
-    if (!id2.c)
-      PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
+    // M1 (L) by F's row permutation: storage only
+    if (!id2.r && (keep & KEEP_L))
+      PLUQ_TRY(permute_rows(c, X(R0, C0, r1, 0), lda, m1 - r1, r1, cr + R0 + r1));
+    // D (rows 0..r1; U, storage only) and H (rows m1..m) by F's column permutation
+    if (!id2.c) {
+      if (keep & KEEP_U)
+        PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, 0, r1, m1, m2, n2, cc + C0 + n1));
+      else
+        PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1), lda, m1, m2, 0, 0, n2, cc + C0 + n1));
+    }
     if (r2 > 0) {
       PLUQ_TRY(trsm_right_upper(c, X(R0, C0, r1, n1), lda, r2, X(R0, C0, m1, n1), lda, m2));
       PLUQ_TRY(fgemm_sub(c, m2, n2 - r2, r2, X(R0, C0, m1, n1), lda, X(R0, C0, r1, n1 + r2), lda,
@@ -493,7 +510,8 @@ struct Recursion {
   // Factors the m x n block at (R0, C0); *r_out receives its rank and *id
   // whether its local row / column index vectors are the identity (then the
   // caller's permutations of the blocks beside it are no-ops and skipped).
-  int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out, Ident* id) {
+  int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out, Ident* id,
+           int keep = KEEP_LU) {
     int32_t* pr = PR(d) + R0;
     int32_t* pc = PC(d) + C0;
     *r_out = 0;
@@ -576,7 +594,7 @@ struct Recursion {
     // A1
     int64_t r1 = 0;
     Ident id1, id2, id3, id4;
-    PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1, &id1));
+    PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1, &id1, KEEP_LU));
     PLUQ_TRY(compose_pair(pr, cr + R0, m1, pc, cc + C0, n1, id1));
     if (!id1.r) PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
     if (!id1.c) PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
@@ -608,17 +626,23 @@ struct Recursion {
                       (m1 - r1) * n2 >= fork_min && m2 * (n1 - r1) >= fork_min;
     if (fork) {
       // F's branch also runs f_post (see there)
-      PLUQ_TRY(fork_fg(R0, C0, m1, n1, m2, n2, r1, d, &r2, &r3, &id2, &id3));
+      PLUQ_TRY(fork_fg(R0, C0, m1, n1, m2, n2, r1, d, &r2, &r3, &id2, &id3, keep));
     } else {
-      PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2, &id2));
-      PLUQ_TRY(f_post(R0, C0, m1, n1, m2, n2, r1, r2, d, id2));
-      PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3, &id3));
+      PLUQ_TRY(node(R0 + r1, C0 + n1, m1 - r1, n2, d + 1, &r2, &id2, keep | KEEP_U));
+      PLUQ_TRY(f_post(R0, C0, m1, n1, m2, n2, r1, r2, d, id2, keep));
+      PLUQ_TRY(node(R0 + m1, C0 + r1, m2, n1 - r1, d + 1, &r3, &id3, keep | KEEP_L));
     }
     PLUQ_TRY(compose_pair(pr + m1, cr + R0 + m1, m2, pc + r1, cc + C0 + r1, n1 - r1, id3));
-    // E (columns 0..r1) and H (columns n1..n) by G's row permutation
-    if (!id3.r)
-      PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
-    if (!id3.c) PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));  // V1
+    // E (columns 0..r1; L, storage only) and H (columns n1..n) by G's row permutation
+    if (!id3.r) {
+      if (keep & KEEP_L)
+        PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, 0, r1, n1, n2, cr + R0 + m1));
+      else
+        PLUQ_TRY(permute_rows2(c, X(R0, C0, m1, 0), lda, m2, n1, n2, 0, 0, cr + R0 + m1));
+    }
+    // V1 (U, storage only) by G's column permutation
+    if (!id3.c && (keep & KEEP_U))
+      PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, r1, n1 - r1, cc + C0 + r1));
 
     // H = [H1 H2; H3 H4] at rows m1.., columns n1.. ([I; K] and H2 are done
     // in f_post): O = L3^{-1} H[:r3, r2:], R -= M3 O
@@ -631,15 +655,17 @@ struct Recursion {
 
     // R
     int64_t r4 = 0;
-    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4, &id4));
+    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4, &id4, keep));
     PLUQ_TRY(compose_pair(pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3, pc + n1 + r2,
                           cc + C0 + n1 + r2, n2 - r2, id4));
-    // E2, M3 (columns 0..r1+r3) and K (columns n1..n1+r2) by R's row permutation
-    if (!id4.r)
+    // E2, M3 (columns 0..r1+r3) and K (columns n1..n1+r2) by R's row
+    // permutation: all L, storage only
+    if (!id4.r && (keep & KEEP_L))
       PLUQ_TRY(permute_rows2(c, X(R0, C0, m1 + r3, 0), lda, m2 - r3, 0, r1 + r3, n1, r2,
                              cr + R0 + m1 + r3));
-    // D2, V2 (rows 0..r1+r2) and O (rows m1..m1+r3) by R's column permutation
-    if (!id4.c)
+    // D2, V2 (rows 0..r1+r2) and O (rows m1..m1+r3) by R's column permutation:
+    // all U, storage only
+    if (!id4.c && (keep & KEEP_U))
       PLUQ_TRY(permute_cols2(c, X(R0, C0, 0, n1 + r2), lda, 0, r1 + r2, m1, r3, n2 - r2,
                              cc + C0 + n1 + r2));
     id->r = id1.r && id2.r && id3.r && id4.r;
@@ -653,7 +679,8 @@ struct Recursion {
         id->r = false;
         const int64_t st[2] = {fr, 0}, ln[2] = {gr, fr};
         PLUQ_TRY(launch_segperm(c, tmp, st, ln, 2));
-        PLUQ_TRY(permute_rows(c, X(R0, C0, a, 0), lda, fr + gr, n, tmp));
+        // (a block whose factors nobody reads needs only its index vectors)
+        if (keep != KEEP_NONE) PLUQ_TRY(permute_rows(c, X(R0, C0, a, 0), lda, fr + gr, n, tmp));
         PLUQ_TRY(launch_compose(c, pr + a, tmp, fr + gr));
       }
     }
@@ -668,7 +695,7 @@ struct Recursion {
         const int64_t ln[4] = {r2, r3, r4, gn};
         const int64_t len = r3 + gn + r2 + r4;
         PLUQ_TRY(launch_segperm(c, tmpc, st, ln, 4));
-        PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, m, len, tmpc));
+        if (keep != KEEP_NONE) PLUQ_TRY(permute_cols(c, X(R0, C0, 0, r1), lda, m, len, tmpc));
         PLUQ_TRY(launch_compose(c, pc + r1, tmpc, len));
       }
     }
@@ -717,7 +744,8 @@ struct TunedScope {
   }
 };
 
-int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t* r_out) {
+int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t* r_out,
+           int keep = KEEP_LU) {
   TunedScope tuned(c, m, n);
   c->mmax = std::max<int64_t>(m, 1);
   c->nmax = std::max<int64_t>(n, 1);
@@ -755,7 +783,7 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
   }
   Recursion rec{c, A, lda, c->small.as<int32_t>() + 8};
   Ident id;
-  PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out, &id));
+  PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out, &id, keep));
   PLUQ_CUDA(cudaMemcpyAsync(c->host_small, c->small.ptr, 32 * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, c->stream));
   PLUQ_CUDA(cudaStreamSynchronize(c->stream));
@@ -849,6 +877,7 @@ int pluq_create(pluq_ctx** ctx, int device) {
   *ctx = nullptr;
   pluq_ctx* c = new pluq_ctx();
   c->device = device;
+  bind_workspace(c);
   if (cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -915,7 +944,8 @@ int rank_profile_modp(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint3
   PLUQ_TRY(prepare(c, p, m, n, form, stream));
   PLUQ_TRY(copy_to_work(c, m, n, A, lda));
   int64_t r = 0;
-  PLUQ_TRY(factor(c, m, n, c->work.as<uint32_t>(), std::max<int64_t>(n, 1), &r));
+  // only the pivots are read: no L or U block needs its final position
+  PLUQ_TRY(factor(c, m, n, c->work.as<uint32_t>(), std::max<int64_t>(n, 1), &r, KEEP_NONE));
   PLUQ_TRY(write_outputs(c, m, n, r, nullptr, nullptr, rank_dev, rrp, crp));
   if (rpm_col_of_row && m > 0) {
     const int32_t* PR = c->perm_r.as<int32_t>();
@@ -934,7 +964,8 @@ static int echelon_core(pluq_ctx* c, int64_t m, int64_t n, uint32_t* W, int64_t 
                         int64_t rs, int64_t cs, int64_t* rank_dev, int32_t* crp,
                         int64_t* r_host = nullptr) {
   int64_t r = 0;
-  PLUQ_TRY(factor(c, m, n, W, ldw, &r));
+  // the echelon form reads U (in the Q frame) and the pivots, never L
+  PLUQ_TRY(factor(c, m, n, W, ldw, &r, KEEP_U));
   if (r_host) *r_host = r;
   PLUQ_TRY(write_outputs(c, m, n, r, nullptr, nullptr, rank_dev, nullptr, nullptr));
   if (r == 0) return PLUQ_OK;
@@ -1292,6 +1323,14 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_TRSM_BLOCK:
       if (value < 1 || value > 64) return PLUQ_ERR_INVALID_ARG;
       c->trsm_block = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_WAIT_LIMIT_US:
+      if (value < 0 || value > 60000000) return PLUQ_ERR_INVALID_ARG;
+      c->wait_cycles = (long long)value * 2000;
+      return PLUQ_OK;
+    case PLUQ_OPT_WORKSPACE_MB:
+      if (value < 0) return PLUQ_ERR_INVALID_ARG;
+      c->ws->limit = (size_t)value << 20;
       return PLUQ_OK;
     default:
       return PLUQ_ERR_INVALID_ARG;

@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kLeafThreads = 512;
 constexpr int kLeafWarps = kLeafThreads / 32;
-constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s
 
 // Grid barrier words and the candidate election of the barrier leaf.  Each
 // CTA writes its candidate (global row index, INT_MAX for none) to its own
@@ -38,7 +37,9 @@ constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s
 constexpr int kLeafMaxCtas = 256;
 struct LeafSync {
   unsigned count;  // grid-barrier arrivals; bit 31: abort
-  int pad[31];
+  int pad0;
+  long long wait_cycles;  // bound of every wait, in SM clock cycles
+  int pad[28];
   int cand[2][kLeafMaxCtas];
 };
 
@@ -74,8 +75,9 @@ __device__ bool grid_barrier(LeafSync* s, unsigned G, unsigned& target, int* err
     target += G;
     unsigned v = atom_add_release(&s->count, 1u) + 1u;
     const long long t0 = clock64();
+    const long long limit = s->wait_cycles;
     while ((v & ~kAbortBit) < target && !(v & kAbortBit)) {
-      if (clock64() - t0 > kBarrierCycles) {
+      if (clock64() - t0 > limit) {
         atomicExch(err, PLUQ_ERR_TIMEOUT);
         atomicOr(&s->count, kAbortBit);
         v = kAbortBit;
@@ -323,8 +325,11 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
   }
 }
 
-__global__ void k_leaf_init(LeafSync* s) {
-  if (threadIdx.x == 0) s->count = 0u;
+__global__ void k_leaf_init(LeafSync* s, long long wait_cycles) {
+  if (threadIdx.x == 0) {
+    s->count = 0u;
+    s->wait_cycles = wait_cycles;
+  }
   for (int i = threadIdx.x; i < kLeafMaxCtas; i += blockDim.x) s->cand[0][i] = s->cand[1][i] = INT_MAX;
 }
 
@@ -370,7 +375,7 @@ int launch_leaf_pluq(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_
   uint32_t* candbuf = reinterpret_cast<uint32_t*>(c->leaf.as<char>() + head);
   {
     ProfScope pi(c, PC_INDEX);
-    k_leaf_init<<<1, 256, 0, c->stream>>>(sync);
+    k_leaf_init<<<1, 256, 0, c->stream>>>(sync, c->wait_cycles);
   }
   int* err = c->small.as<int>() + 16;
   const uint32_t* tab = inv_table_ptr(c);
@@ -400,7 +405,9 @@ namespace {
 struct ChainSync {
   unsigned long long word;
   int abort;
-  int pad[61];
+  int pad0;
+  long long wait_cycles;  // bound of every wait, in SM clock cycles
+  int pad[58];
 };
 
 struct PivInfo {
@@ -476,12 +483,13 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
     if (tid == 0) {
       unsigned long long w = chain_acquire(&sync->word);
       const long long t0 = clock64();
+      const long long limit = sync->wait_cycles;
       bool ok = true;
       // the abort flag is an error path: checked every 32nd poll only, so a
       // poll is one L2 round trip
       for (unsigned it = 1; (int)(w >> 32) < need_done && (int)(w & 0xffffffffu) < need_piv;
            ++it) {
-        if ((it & 31u) == 0 && (ld_volatile_i(&sync->abort) || clock64() - t0 > kBarrierCycles)) {
+        if ((it & 31u) == 0 && (ld_volatile_i(&sync->abort) || clock64() - t0 > limit)) {
           if (!ld_volatile_i(&sync->abort)) atomicExch(err, PLUQ_ERR_TIMEOUT);
           atomicExch(&sync->abort, 1);
           ok = false;
@@ -654,9 +662,10 @@ __global__ void __launch_bounds__(kLeafThreads, 1)
   }
 }
 
-__global__ void k_chain_init(ChainSync* s) {
+__global__ void k_chain_init(ChainSync* s, long long wait_cycles) {
   s->word = 0ull;
   s->abort = 0;
+  s->wait_cycles = wait_cycles;
 }
 
 size_t chain_smem(int m, int n, int R) {
@@ -704,7 +713,7 @@ int launch_leaf_chain(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32
   uint32_t* pub = reinterpret_cast<uint32_t*>(c->leaf.as<char>() + head + sizeof(PivInfo) * mn);
   {
     ProfScope pi(c, PC_INDEX);
-    k_chain_init<<<1, 1, 0, c->stream>>>(sync);
+    k_chain_init<<<1, 1, 0, c->stream>>>(sync, c->wait_cycles);
   }
   int* err = c->small.as<int>() + 16;
   const uint32_t* tab = inv_table_ptr(c);

@@ -454,7 +454,73 @@ def test_rank_profile_parity(ctx, p):
     assert rpm.cpu().numpy().tolist() == expect.tolist()
 
 
+@pytest.mark.parametrize("leaf", [(96, 3), (96, 0), (96, 1), (0, 0)])
+@pytest.mark.parametrize("fork_depth", [0, 2])
+@pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
+                                          (65521, (900, 500), 0.3)])
+def test_rank_and_echelon_fast_paths_deep(ctx, leaf, fork_depth, p, shape, frac):
+    """rank_profile_modp (no L or U kept) and echelon_modp (U only) skip the
+    permutations of blocks whose factors they never read; through a deep
+    recursion with rank-deficient blocks both still equal the oracle."""
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(frac * min(m, n)), p, seed=11)
+    ctx.set_option("fork_depth", fork_depth)
+    try:
+        with leaf_mode(ctx, leaf, tiles=(32, 32)):
+            r, rrp, crp, rpm = pq.rank_profile_modp(to_dev(g.A), p, ctx=ctx)
+            r2, R, crp2 = pq.echelon_modp(to_dev(g.A), p, ctx=ctx)
+            torch.cuda.synchronize()
+    finally:
+        ctx.set_option("fork_depth", 2)
+    assert r == r2 == g.rank
+    assert rrp.cpu().tolist() == g.rrp.tolist() and crp.cpu().tolist() == g.crp.tolist()
+    expect = np.full(m, -1)
+    expect[g.rows] = g.cols
+    assert rpm.cpu().numpy().tolist() == expect.tolist()
+    rr, Rref = oracle.rref(g.A, p)
+    assert crp2.cpu().tolist() == g.crp.tolist()
+    assert np.array_equal(R.cpu().numpy().astype(np.int64), Rref.astype(np.int64))
+
+
 # ------------------------------------------------------------- errors --
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_wait_limit_runs_out(kind):
+    """A cooperative leaf whose spin-waits are given no time returns
+    PLUQ_ERR_TIMEOUT (every CTA leaves, nothing faults), and the same context
+    then factors the matrix exactly once the limit is restored."""
+    c = pq.Context(0)
+    try:
+        p = 131071
+        A = workloads.uniform_matrix(700, 700, p, 9)
+        c.set_option("leaf_dim", 1024)
+        c.set_option("leaf_kind", kind)
+        c.set_option("wait_limit_us", 0)
+        with pytest.raises(pq.PluqError) as e:
+            pq.pluq_modp(to_dev(A), p, ctx=c)
+        assert e.value.status == -8  # PLUQ_ERR_TIMEOUT
+        c.set_option("wait_limit_us", 2000000)
+        assert_parity(c, A, p)
+    finally:
+        c.close()
+
+
+def test_workspace_cap():
+    """A workspace cap below what a call needs gives PLUQ_ERR_NO_WORKSPACE; lifting it
+    lets the same context factor the matrix."""
+    c = pq.Context(0)
+    try:
+        p = 65521
+        A = workloads.uniform_matrix(1500, 1400, p, 4)
+        c.set_option("workspace_mb", 1)
+        with pytest.raises(pq.PluqError) as e:
+            pq.pluq_modp(to_dev(A), p, ctx=c)
+        assert e.value.status == -6  # PLUQ_ERR_NO_WORKSPACE
+        c.set_option("workspace_mb", 0)
+        assert_parity(c, A, p)
+    finally:
+        c.close()
+
 
 def test_status_codes(ctx):
     A = to_dev(np.ones((4, 4)))
