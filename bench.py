@@ -254,8 +254,21 @@ def time_steps(pq, ctx, A, A0, p, form, steps, stream):
     return start.elapsed_time(stop) / steps
 
 
+def batch_shard(cfg, rank: int):
+    """Shard `rank` of the batched workload across GPUs: its own batch of cfg.count
+    matrices of the workload's distribution (shard 0 is the workload itself), so the
+    global batch grows with the number of ranks and no data crosses between them.
+
+    Returns (tag, m, n, r): the generator tag of the shard's matrices and their shapes.
+    """
+    tag = "batched" if rank == 0 else f"batched-shard{rank}"
+    ms, ns, rs = workloads.batched_shapes(cfg.count, cfg.lo, cfg.hi, seed=1, tag=tag)
+    return tag, ms, ns, rs
+
+
 def bench_batched(args, world, rank, local):
-    """Many small rank-deficient matrices in one persistent graph-captured launch."""
+    """Many small rank-deficient matrices in one persistent graph-captured launch;
+    several GPUs each factor their own shard of the global batch (weak scaling)."""
     import torch
     import paper_1402_3501_gb300 as pq
 
@@ -266,9 +279,9 @@ def bench_batched(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cfg = workloads.CONFIGS[args.workload]
     p = cfg.p
-    ms, ns, rs = workloads.batched_shapes(cfg.count, cfg.lo, cfg.hi, seed=1)
+    tag, ms, ns, rs = batch_shard(cfg, rank)
     gens = [workloads.prescribed_rank_matrix(int(ms[b]), int(ns[b]), int(rs[b]), p, seed=1,
-                                             tag=f"batched:{b}", device="cuda")
+                                             tag=f"{tag}:{b}", device="cuda")
             for b in range(cfg.count)]
     sizes = [int(g.A.size) for g in gens]
     offs = np.concatenate([[0], np.cumsum(sizes)])
@@ -314,7 +327,7 @@ def bench_batched(args, world, rank, local):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "count": cfg.count, "m_n_range": [cfg.lo, cfg.hi],
                        "p": p, "step": "restore inputs (D2D copy) + pluq_modp_batched",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"batch sharded x{world} ({cfg.count} matrices a rank)"},
             "bitexact": bool(exact),
             "matrices_per_s": round(world * cfg.count / (ms_step / 1e3), 1),
             "per_matrix_launches": {"ms_per_matrix": round(per_ms, 4),

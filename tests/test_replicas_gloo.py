@@ -94,3 +94,53 @@ def test_dead_replica_is_reported():
     assert not any(alive)
     assert procs[1].exitcode == 3 and res[1] == "left"
     assert res[0][0] != "no error" and res[0][1] < 60
+
+
+def _shard_main(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import workloads
+    cfg = workloads.CONFIGS["batched-4096-lru-p65521"]
+    tag, ms, ns, rs = bench.batch_shard(cfg, rank)
+    # each rank factors a few of its own matrices (the oracle stands in for the GPU)
+    import oracle
+    ok = True
+    for b in range(3):
+        g = workloads.prescribed_rank_matrix(int(ms[b]), int(ns[b]), int(rs[b]), cfg.p, seed=1,
+                                             tag=f"{tag}:{b}")
+        res = oracle.pluq(g.A, cfg.p, want_lu=False)
+        ok &= res.rank == g.rank and res.rpm == g.rpm
+    shapes = [None] * world
+    dist.all_gather_object(shapes, (tag, ms.tolist(), ns.tolist(), rs.tolist()))
+    local_ms = 5.0 + rank
+    slowest = bench.max_over_ranks(local_ms, dist, "cpu")
+    out[rank] = (ok, shapes, slowest)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batched_shards_gloo():
+    """The batched workload sharded over two ranks: shard 0 is the single-GPU workload
+    itself, shard 1 a distinct batch of the same distribution, each rank factors its
+    own matrices with no collective on the data path, and the whole-job figure takes
+    all ranks' matrices over the slowest rank's time."""
+    import workloads
+    world = 2
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_shard_main, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0][0] and res[1][0]
+    shapes = res[0][1]
+    cfg = workloads.CONFIGS["batched-4096-lru-p65521"]
+    ms, ns, rs = workloads.batched_shapes(cfg.count, cfg.lo, cfg.hi, seed=1)
+    assert shapes[0][1:] == (ms.tolist(), ns.tolist(), rs.tolist())  # shard 0 = the workload
+    assert shapes[0][0] != shapes[1][0] and shapes[0][1:] != shapes[1][1:]
+    for tag, m, n, r in shapes:
+        assert len(m) == cfg.count
+        assert all(cfg.lo <= x <= cfg.hi for x in m + n)
+        assert all(1 <= rr <= min(a, b) for rr, a, b in zip(r, m, n))
+    assert res[0][2] == res[1][2] == 6.0
