@@ -290,6 +290,13 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        every CTA of the launch returns, the call returns
  *                        that status and the context stays usable.  0 makes
  *                        any wait that is not satisfied at once run out.
+ *   PLUQ_OPT_WINOGRAD_MIN  [0, 2^31): Schur updates whose M, N and K are all at
+ *                        least this value take a Strassen-Winograd level
+ *                        (Sec. 2.3 and Sec. 3.2: seven half-size products and
+ *                        fifteen additions mod p instead of eight products),
+ *                        recursively while the halves still qualify; 0
+ *                        (default): classical products only.  Results are
+ *                        identical (the pre-additions are reduced mod p).
  *   PLUQ_OPT_WORKSPACE_MB  cap on the device workspace the context (with its
  *                        child contexts) holds, in MiB [0, 2^31); 0 (default):
  *                        none.  A call whose workspace would exceed the cap
@@ -309,6 +316,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_SLAB_ROWS 11
 #define PLUQ_OPT_WAIT_LIMIT_US 12
 #define PLUQ_OPT_WORKSPACE_MB 13
+#define PLUQ_OPT_WINOGRAD_MIN 14
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

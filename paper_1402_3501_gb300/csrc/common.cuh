@@ -211,6 +211,12 @@ struct pluq_ctx {
   int use_tuned = 1;
   bool tuning = false;            // inside pluq_autotune: candidates set explicitly
   DevBuf tune_src, tune_dst;      // the caller's matrix and a trial copy
+  // Strassen-Winograd levels above the fgemm: applied while M, N, K are all at
+  // least wino_min (0: never); pre-additions and partial sums in `wino`, one
+  // region a level from offset wino_used
+  int64_t wino_min = 0;
+  DevBuf wino;
+  int64_t wino_used = 0;
   // per-call statistics (host side)
   int64_t n_base = 0, n_nodes = 0, n_gemm = 0;
   // device error flag (int) lives in small at offset 0
@@ -220,7 +226,7 @@ struct pluq_ctx {
 inline void bind_workspace(pluq_ctx* c) {
   for (DevBuf* b : {&c->scratch, &c->pack, &c->perm_r, &c->perm_c, &c->tmp_i, &c->tri_inv,
                     &c->small, &c->inv_table, &c->work, &c->leaf, &c->batch_dev,
-                    &c->batch_scratch, &c->batch_pq, &c->tune_src, &c->tune_dst})
+                    &c->batch_scratch, &c->batch_pq, &c->tune_src, &c->tune_dst, &c->wino})
     b->acct = c->ws;
 }
 
@@ -282,6 +288,14 @@ int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint
 // C <- C - A B (mod p); A M x K, B K x N, C M x N, all row-major uint32.
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
+// fgemm_sub without the Winograd levels (thin, limb or FP64 by form)
+int fgemm_sub_classical(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+                        int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);
+// one Strassen-Winograd level (then recursively while wino_applies) over
+// fgemm_sub_classical; depth counts the levels above
+int wino_applies(const pluq_ctx* c, int64_t M, int64_t N, int64_t K);
+int fgemm_sub_wino(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
+                   const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc, int depth);
 // the same on the CUDA cores for a thin inner dimension (K <= kThinMaxK,
 // K p < 2^31) and small total work
 constexpr int64_t kThinMaxK = 128;

@@ -283,6 +283,7 @@ void destroy_lane(pluq_ctx* l) {
   l->small.release();
   l->leaf.release();
   l->work.release();
+  l->wino.release();
   for (cudaEvent_t e : l->prof.pool) cudaEventDestroy(e);
   if (l->fork_ev) cudaEventDestroy(l->fork_ev);
   for (cudaEvent_t e : l->side_ev)
@@ -313,6 +314,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->stream = l->own_stream;
   l->sm_count = std::max(1, c->sm_count / 2);
   l->wait_cycles = c->wait_cycles;
+  l->wino_min = c->wino_min;
   l->F = c->F;
   l->form = c->form;
   l->bm = c->bm;
@@ -860,6 +862,13 @@ int check_prime_range(uint32_t p) { return check_p(p); }
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
+  if (wino_applies(c, M, N, K)) return fgemm_sub_wino(c, M, N, K, A, lda, B, ldb, C, ldc, 0);
+  return fgemm_sub_classical(c, M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+int fgemm_sub_classical(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A,
+                        int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
+  if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
   c->n_gemm++;
   if (c->form == PLUQ_FORM_LIMB_F16) {
     // a thin inner dimension does not pay for packing and a tensor pipeline
@@ -920,6 +929,7 @@ int pluq_destroy(pluq_ctx* c) {
   if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
   if (c->batch_host) cudaFreeHost(c->batch_host);
   c->work.release();
+  c->wino.release();
   if (c->host_small) cudaFreeHost(c->host_small);
   delete c;
   return PLUQ_OK;
@@ -1327,6 +1337,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_WAIT_LIMIT_US:
       if (value < 0 || value > 60000000) return PLUQ_ERR_INVALID_ARG;
       c->wait_cycles = (long long)value * 2000;
+      return PLUQ_OK;
+    case PLUQ_OPT_WINOGRAD_MIN:
+      if (value < 0) return PLUQ_ERR_INVALID_ARG;
+      c->wino_min = value;
       return PLUQ_OK;
     case PLUQ_OPT_WORKSPACE_MB:
       if (value < 0) return PLUQ_ERR_INVALID_ARG;

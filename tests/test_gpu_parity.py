@@ -172,6 +172,45 @@ def test_fgemm_large_primes_extremes(ctx, p):
                 assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), (form, a, b, K)
 
 
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("p", [2, 65521, 131071, 2147483647])
+@pytest.mark.parametrize("mnk", [(256, 256, 256), (301, 259, 333), (520, 130, 777)])
+def test_fgemm_winograd_levels(ctx, form, p, mnk):
+    """Strassen-Winograd levels (forced down to small sizes, odd dimensions
+    peeled) give exactly C - A B mod p, as the classical product does."""
+    M, N, K = mnk
+    rng = np.random.default_rng(M + N + K + p % 101)
+    A = rng.integers(0, p, (M, K), dtype=np.int64)
+    B = rng.integers(0, p, (K, N), dtype=np.int64)
+    C = rng.integers(0, p, (M, N), dtype=np.int64)
+    A[0, :] = p - 1
+    B[:, -1] = p - 1
+    expect = (C - matmul_mod(A, B, p)) % p
+    for wmin in (64, 100):
+        ctx.set_option("winograd_min", wmin)
+        try:
+            Cd = to_dev(C)
+            pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form=form, ctx=ctx)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_option("winograd_min", 0)
+        assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect), wmin
+
+
+@pytest.mark.parametrize("p,shape,frac", [(65521, (900, 900), 1.0), (131071, (777, 700), 0.6)])
+def test_pluq_winograd_levels(ctx, p, shape, frac):
+    """The factorization with Winograd levels in its Schur updates equals the oracle."""
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(frac * min(m, n)), p, seed=8)
+    ctx.set_option("winograd_min", 96)
+    try:
+        with leaf_mode(ctx, (128, 3)):
+            assert_parity(ctx, g.A, p, "limb")
+            assert_parity(ctx, g.A, p, "fp64")
+    finally:
+        ctx.set_option("winograd_min", 0)
+
+
 def test_fgemm_strided_views(ctx):
     p = 131071
     rng = np.random.default_rng(3)
