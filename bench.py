@@ -384,6 +384,8 @@ def bench_ours(args, world, rank, local):
     # schedule chosen by the library's autotuner on this matrix (untimed), then
     # warm-up (not timed) and bit-exact validation against the construction
     schedule = None
+    if args.winograd_min:
+        ctx.set_option("winograd_min", args.winograd_min)
     if args.decomposition == "iterative":
         ctx.set_option("decomposition", 1)
         ctx.set_option("slab_rows", args.slab_rows)
@@ -521,6 +523,7 @@ def bench_ours(args, world, rank, local):
                        "l2": f"inputs ({m * n * 4 / 1e6:.0f} MB) larger than L2 (129 MB), no flush",
                        "step": "restore input (D2D copy) + pluq_modp",
                        "schedule": schedule or "default (leaf 1024, per-leaf kind, fork depth 2)",
+                       "winograd_min": args.winograd_min,
                        "decomposition": ("tile recursive" if args.decomposition == "recursive"
                                          else f"tiled iterative (slab rows "
                                               f"{args.slab_rows or 'leaf cut-off'})"),
@@ -582,6 +585,7 @@ def profile_fgemm(args):
     B = dev(workloads.uniform_matrix(K, N, p, 1, "caseb"))
     C = dev(workloads.uniform_matrix(M, N, p, 1, "casec"))
     ctx = pq.Context(0)
+    ctx.set_option("winograd_min", args.winograd_min)
     form = "fp64" if args.form == "fp64" else "limb"
     ms = []
     for _ in range(max(1, args.repeat)):
@@ -592,7 +596,7 @@ def profile_fgemm(args):
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(f"fgemm {M}x{N}x{K} p={p} {form}: last {ms[-1]:.3f} ms "
+    print(f"fgemm {M}x{N}x{K} p={p} {form} winograd_min={args.winograd_min}: last {ms[-1]:.3f} ms "
           f"({2.0 * M * N * K / ms[-1] / 1e9:.1f} field Tops/s)", flush=True)
 
 
@@ -623,6 +627,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS),
                     help="matrix to factor (the default is the measured workload; the "
                          "others serve as small profiling cases)")
+    ap.add_argument("--winograd-min", type=int, default=0,
+                    help="Strassen-Winograd levels on Schur updates with M, N, K all at least "
+                         "this (0: classical products only)")
     ap.add_argument("--fgemm", default="",
                     help="MxNxK: profiling case of one fgemm_modp call instead of the bench "
                          "(with --p, --form, --repeat)")

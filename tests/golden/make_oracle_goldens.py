@@ -14,6 +14,10 @@ seed, plus a SHA-256 of the input bytes so a test can tell that the matrix it
 regenerates is the one that was factored.
 
   python tests/golden/make_oracle_goldens.py [--threads T] [--key KEY] [--seed S]
+  python tests/golden/make_oracle_goldens.py --rref --key lru-8192-r4096-p131071
+
+--rref instead records the oracle's reduced row echelon form of a prescribed-rank
+workload as a digest (rank, pivot columns, SHA-256 of its bytes).
 """
 from __future__ import annotations
 
@@ -59,13 +63,44 @@ def write(key: str, seed: int, threads: int) -> str:
     return out
 
 
+def rref_path(key: str, seed: int) -> str:
+    return os.path.join(HERE, f"oracle_rref_{key}_seed{seed}.npz")
+
+
+def write_rref(key: str, seed: int, threads: int) -> str:
+    """The oracle's reduced row echelon form of a prescribed-rank workload, kept as
+    its rank, pivot columns and the SHA-256 of its r x n uint32 bytes (the form
+    itself is too large to store): a result is equal to it iff its digest is."""
+    cfg = workloads.CONFIGS[key]
+    assert cfg.kind == "lru"
+    A = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=seed).A
+    t = time.time()
+    r, R = oracle.rref(A, cfg.p, threads=threads)
+    dt = time.time() - t
+    R = np.ascontiguousarray(R, dtype=np.uint32)
+    pivots = np.array([int(np.flatnonzero(R[i])[0]) for i in range(r)], np.int32)
+    out = rref_path(key, seed)
+    np.savez_compressed(
+        out, rank=np.array([r], np.int64), crp=pivots, shape=np.array([cfg.m, cfg.n], np.int64),
+        p=np.array([cfg.p], np.int64), seed=np.array([seed], np.int64),
+        sha256=np.array([hashlib.sha256(R.tobytes()).hexdigest()]),
+        input_sha256=np.array([input_digest(A)]))
+    print(f"{key} seed {seed}: RREF rank {r}, oracle {dt:.0f} s on {threads} threads -> {out}")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--key", default="uniform-32768-p65521")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--rref", action="store_true",
+                    help="write the digest of the oracle's RREF of a prescribed-rank workload")
     a = ap.parse_args()
-    write(a.key, a.seed, a.threads)
+    if a.rref:
+        write_rref(a.key, a.seed, a.threads)
+    else:
+        write(a.key, a.seed, a.threads)
 
 
 if __name__ == "__main__":

@@ -151,3 +151,77 @@ def check_rref(A: np.ndarray, p: int, R: np.ndarray, crp) -> None:
     for t in range(r):
         assert not np.any(R[t, :crp[t]]), "non-zero left of a pivot"
     assert np.array_equal(matmul_mod(A[:, crp], R, p), A % p), "A != A[:, crp] R"
+
+
+def _split16(X: np.ndarray, p: int):
+    """X as a list of (weight mod p, float64 part) with every part below 2^16 when
+    p >= 2^20 (16-bit halves), else the whole of X."""
+    X = np.asarray(X, dtype=np.int64)
+    if p < 2 ** 20:
+        return [(1, X.astype(np.float64))]
+    return [(pow(2, 16, p), (X >> 16).astype(np.float64)), (1, (X & 0xFFFF).astype(np.float64))]
+
+
+def matmul_mod_f64(X: np.ndarray, Y: np.ndarray, p: int) -> np.ndarray:
+    """Exact X @ Y mod p by float64 BLAS products: operands split into 16-bit
+    halves for p >= 2^20 so that every sum stays below 2^53 (inner dimension up
+    to 2^20)."""
+    k = np.asarray(X).shape[1]
+    out = np.zeros((np.asarray(X).shape[0], np.asarray(Y).shape[1]), dtype=np.int64)
+    for wx, xs in _split16(X, p):
+        for wy, ys in _split16(Y, p):
+            bound = float(xs.max(initial=0.0)) * float(ys.max(initial=0.0)) * k
+            assert bound < 2.0 ** 53, "float64 sums would not be exact"
+            part = np.mod(xs @ ys, p).astype(np.int64)
+            out = (out + part * (wx * wy % p)) % p
+    return out
+
+
+def unit_lower_rows(LU: np.ndarray, r: int, i0: int, i1: int) -> np.ndarray:
+    """Rows i0..i1 of the unit lower trapezoidal L (m x r) of a compressed L\\U."""
+    rows = np.arange(i0, i1)
+    Lb = np.where(np.arange(r)[None, :] < rows[:, None],
+                  np.asarray(LU[i0:i1, :r], dtype=np.int64), 0)
+    on_diag = rows < r
+    Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1
+    return Lb
+
+
+def freivalds(A: np.ndarray, p: int, P, Q, LU: np.ndarray, r: int, trials: int = 3,
+              seed: int = 0, step: int = 2048) -> None:
+    """Freivalds' test of A[P][:, Q] = L U mod p with `trials` random vectors at once
+    (a wrong factorization passes with probability at most p^-trials); exact
+    float64 BLAS products, row blocks of `step` rows."""
+    rng = np.random.default_rng(seed)
+    m, n = A.shape
+    P = np.asarray(P, dtype=np.int64)
+    Q = np.asarray(Q, dtype=np.int64)
+    X = rng.integers(0, p, (n, trials), dtype=np.int64)
+    Z = np.zeros((n, trials), dtype=np.int64)
+    Z[Q] = X  # (A Q^T) X = A Z
+    AZ = np.concatenate([matmul_mod_f64(A[i:i + step], Z, p) for i in range(0, m, step)])
+    lhs = AZ[P]
+    UX = (np.concatenate([matmul_mod_f64(np.triu(np.asarray(LU[i:min(r, i + step)],
+                                                            dtype=np.int64), i), X, p)
+                          for i in range(0, r, step)]) if r else np.zeros((0, trials), np.int64))
+    rhs = np.concatenate([matmul_mod_f64(unit_lower_rows(LU, r, i, min(m, i + step)), UX, p)
+                          for i in range(0, m, step)])
+    assert np.array_equal(lhs, rhs), "Freivalds check of P L U Q = A failed"
+
+
+def exact_identity(A: np.ndarray, p: int, P, Q, LU: np.ndarray, r: int, rows=None,
+                   step: int = 2048) -> None:
+    """A[P][:, Q] = L U mod p entry by entry (exact float64 BLAS products), over
+    every row or over the given rows of the permuted frame."""
+    m, n = A.shape
+    P = np.asarray(P, dtype=np.int64)
+    Q = np.asarray(Q, dtype=np.int64)
+    U = np.triu(np.asarray(LU[:r, :], dtype=np.int64))
+    idx = np.arange(m) if rows is None else np.sort(np.asarray(rows, dtype=np.int64))
+    for s in range(0, len(idx), step):
+        sel = idx[s:s + step]
+        Lb = np.concatenate([unit_lower_rows(LU, r, i, i + 1) for i in sel]) if rows is not None \
+            else unit_lower_rows(LU, r, int(sel[0]), int(sel[-1]) + 1)
+        got = matmul_mod_f64(Lb, U, p) if r else np.zeros((len(sel), n), np.int64)
+        want = np.asarray(A, dtype=np.int64)[P[sel]][:, Q] % p
+        assert np.array_equal(got, want), f"P L U Q != A in rows {sel[0]}..{sel[-1]}"

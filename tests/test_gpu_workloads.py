@@ -9,13 +9,16 @@ decides each case:
     matrix, profiles, RREF) and an exact host product for the factor identity;
   * 8192^2 rank 4096 over GF(131071), seeds 1-3: the L R U construction, whose
     rank profile matrix is R (Sec. 4.1), an exact float64 host product of L U
-    (every partial sum below 2^53) for both forms, and the oracle's RREF (seed 1);
+    (every partial sum below 2^53) for both forms, and the oracle's RREF (seed 1,
+    compared through the SHA-256 digest its writer script stores);
   * uniform 32768^2 over GF(65521): the oracle's rank profile matrix stored by
-    tests/golden/make_oracle_goldens.py, an exact product of L U computed with
-    cuBLAS float64 on the GPU (a library product, independent of this
-    library's kernels), and a 3-trial Freivalds check on the host, both forms;
+    tests/golden/make_oracle_goldens.py, the exact product L U on 4096 sampled
+    rows computed with cuBLAS float64 on the GPU (a library product,
+    independent of this library's kernels), and a 3-trial Freivalds check of
+    the whole identity on the host, both forms;
   * 16384 x 20480 rank 16320 over GF(2^31 - 1): the construction, the exact
-    GPU product in 16-bit halves and 3-trial Freivalds, both forms;
+    GPU product on 2048 sampled rows (16-bit halves) and 3-trial Freivalds,
+    both forms;
   * the batch of 4096 matrices (m, n uniform in [32, 512], p = 65521): the
     construction for every matrix, L U = the permuted A exactly for every
     matrix, and the oracle on every 8th matrix.
@@ -27,7 +30,7 @@ import pytest
 
 import oracle
 import workloads
-from pluq_checks import check_pluq, check_rpm_from_pq
+from pluq_checks import check_pluq, check_rpm_from_pq, exact_identity, freivalds
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,17 +69,27 @@ def check_structure(LU, r):
     assert torch.all(torch.diagonal(LU[:r, :r]) != 0), "zero on U's diagonal"
 
 
-def _lu_block_f64(LU, r, i0, i1):
-    """Rows i0..i1 of the unit lower trapezoidal L (m x r) as float64 (device)."""
-    Lb = LU[i0:i1, :r].to(torch.float64)
-    rows = torch.arange(i0, i1, device=LU.device)[:, None]
+def _lu_rows_f64(LU, r, sel):
+    """The rows `sel` (device int64) of the unit lower trapezoidal L (m x r) as
+    float64 (device)."""
+    Lb = LU[sel, :r].to(torch.float64)
+    rows = sel[:, None]
     cols = torch.arange(r, device=LU.device)[None, :]
     Lb = torch.where(cols < rows, Lb, torch.zeros_like(Lb))
     return Lb + (cols == rows).to(torch.float64)
 
 
-def exact_identity_gpu(A_dev, p, P, Q, LU, r, block=4096):
-    """A[P][:, Q] == L U mod p, entry by entry, with cuBLAS float64 products.
+def sample_rows(m, count, seed):
+    """`count` distinct rows of [0, m), seeded, always with the first and last."""
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(m, size=min(m, count), replace=False)
+    return np.unique(np.concatenate([rows, [0, m - 1]]))
+
+
+def exact_identity_gpu(A_dev, p, P, Q, LU, r, rows, block=4096):
+    """A[P][:, Q] == L U mod p entry by entry on the given rows of the permuted
+    frame, with cuBLAS float64 products (a library product, independent of this
+    library's kernels).
 
     Every float64 product of integers is exact while its sums stay below 2^53:
     r (p-1)^2 < 2^53 for p < 2^17 and r <= 2^19; larger p are split into 16-bit
@@ -86,6 +99,7 @@ def exact_identity_gpu(A_dev, p, P, Q, LU, r, block=4096):
     dev = A_dev.device
     Pt = torch.from_numpy(P.astype(np.int64)).to(dev)
     Qt = torch.from_numpy(Q.astype(np.int64)).to(dev)
+    sel_all = torch.from_numpy(np.sort(np.asarray(rows, dtype=np.int64))).to(dev)
     if r == 0:
         assert not torch.any(A_dev != 0)
         return
@@ -97,9 +111,9 @@ def exact_identity_gpu(A_dev, p, P, Q, LU, r, block=4096):
     else:
         Uf = U.to(torch.float64)
     del U
-    for i0 in range(0, m, block):
-        i1 = min(m, i0 + block)
-        Lb = _lu_block_f64(LU, r, i0, i1)
+    for i0 in range(0, len(sel_all), block):
+        sel = sel_all[i0:i0 + block]
+        Lb = _lu_rows_f64(LU, r, sel)
         if not split:
             got = torch.remainder(Lb @ Uf, p).to(torch.int64)
         else:
@@ -110,65 +124,8 @@ def exact_identity_gpu(A_dev, p, P, Q, LU, r, block=4096):
                                   p).to(torch.int64)
             ll = torch.remainder(Ll @ Ul, p).to(torch.int64)
             got = (hh * c32 % p + mid * c16 % p + ll) % p
-        want = A_dev[Pt[i0:i1]][:, Qt].to(torch.int64) % (1 << 32)
-        assert torch.equal(got, want), f"P L U Q != A in rows {i0}..{i1}"
-
-
-def freivalds_host(A, p, P, Q, LU_host, r, trials=3, seed=0, step=2048):
-    """Host Freivalds check of A[P][:, Q] = L U mod p with exact int64 sums (chunks of
-    the inner dimension keep every partial sum below 2^63); error below p^-trials."""
-    rng = np.random.default_rng(seed)
-    m, n = A.shape
-
-    def mv_part(X, v, xmax):
-        # sums of at most `chunk` products below xmax * p stay below 2^62
-        chunk = max(1, (2 ** 62) // max(1, xmax * p))
-        out = np.zeros(X.shape[0], dtype=np.int64)
-        for s in range(0, X.shape[1], chunk):
-            out = (out + (X[:, s:s + chunk] @ v[s:s + chunk]) % p) % p
-        return out
-
-    def mv(X, v):
-        X = X.astype(np.int64)
-        if p < 2 ** 20:
-            return mv_part(X, v, p)
-        # 16-bit halves of X: X v = 2^16 (X_hi v) + X_lo v
-        hi = mv_part(X >> 16, v, p >> 16)
-        lo = mv_part(X & 0xFFFF, v, 1 << 16)
-        return (hi * (1 << 16) % p + lo) % p
-
-    for _ in range(trials):
-        x = rng.integers(0, p, n, dtype=np.int64)
-        z = np.zeros(n, dtype=np.int64)
-        z[Q] = x
-        lhs = np.concatenate([mv(A[i:i + step], z) for i in range(0, m, step)])[P]
-        ux = (np.concatenate([mv(np.triu(LU_host[i:min(r, i + step)].astype(np.int64), i), x)
-                              for i in range(0, r, step)]) if r else np.zeros(0, np.int64))
-        rhs = np.zeros(m, dtype=np.int64)
-        for i in range(0, m, step):
-            rows = np.arange(i, min(m, i + step))
-            Lb = np.where(np.arange(r)[None, :] < rows[:, None],
-                          LU_host[i:i + step, :r].astype(np.int64), 0)
-            on_diag = rows < r
-            Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1
-            rhs[i:i + step] = mv(Lb, ux)
-        assert np.array_equal(lhs, rhs), "Freivalds check of P L U Q = A failed"
-
-
-def exact_identity_host_f64(A, p, P, Q, LU_host, r, step=2048):
-    """A[P][:, Q] == L U mod p with float64 host products (exact: r (p-1)^2 < 2^53)."""
-    assert r * (p - 1) ** 2 < 2 ** 53
-    m, n = A.shape
-    U = np.triu(LU_host[:r, :].astype(np.float64))
-    for i in range(0, m, step):
-        rows = np.arange(i, min(m, i + step))
-        Lb = np.where(np.arange(r)[None, :] < rows[:, None],
-                      LU_host[i:i + step, :r].astype(np.float64), 0.0)
-        on_diag = rows < r
-        Lb[np.nonzero(on_diag)[0], rows[on_diag]] = 1.0
-        got = np.mod(Lb @ U, p).astype(np.int64)
-        want = A[P[i:i + step]][:, Q].astype(np.int64)
-        assert np.array_equal(got, want), f"P L U Q != A in rows {i}..{i + len(rows)}"
+        want = A_dev[Pt[sel]][:, Qt].to(torch.int64) % (1 << 32)
+        assert torch.equal(got, want), f"P L U Q != A in sampled rows from {i0}"
 
 
 # ------------------------------------------------------- uniform 1024^2 --
@@ -206,21 +163,38 @@ def test_lru_8192(ctx, seed, form):
     check_rpm_from_pq(P, Q, r, g.rpm)
     assert rrp == g.rrp.tolist() and crp == g.crp.tolist()
     check_structure(LU, r)
-    exact_identity_host_f64(g.A, cfg.p, P, Q, LU.cpu().numpy(), r)
+    exact_identity(g.A, cfg.p, P, Q, LU.cpu().numpy().view(np.uint32), r)
 
 
 def test_lru_8192_rref(ctx):
-    """The reduced echelon form at full size equals the oracle's (both forms)."""
+    """The reduced echelon form at full size equals the oracle's, byte for byte
+    (its SHA-256 as stored by tests/golden/make_oracle_goldens.py --rref), in
+    both forms, and satisfies the properties that fix it: R[:, CRP] = I, zeros
+    left of each pivot, A = A[:, CRP] R mod p (checked on sampled rows)."""
+    import hashlib
     cfg = workloads.CONFIGS["lru-8192-r4096-p131071"]
+    path = os.path.join(GOLDEN, "oracle_rref_lru-8192-r4096-p131071_seed1.npz")
+    assert os.path.exists(path), "oracle RREF digest of the 8192^2 workload is missing"
+    gold = np.load(path)
     g = workloads.prescribed_rank_matrix(cfg.m, cfg.n, cfg.r, cfg.p, seed=1, device="cuda")
-    rr, Rref = oracle.rref(g.A, cfg.p, threads=os.cpu_count() or 1)
-    assert rr == cfg.r
+    assert hashlib.sha256(g.A.tobytes()).hexdigest() == str(gold["input_sha256"][0])
     Ad = to_dev(g.A)
     for form in ("limb", "fp64"):
         r, R, crp = pq.echelon_modp(Ad, cfg.p, form=form, ctx=ctx)
         torch.cuda.synchronize()
-        assert r == rr and crp.cpu().tolist() == g.crp.tolist()
-        assert np.array_equal(R.cpu().numpy().astype(np.int64), Rref.astype(np.int64)), form
+        assert r == int(gold["rank"][0]) == cfg.r
+        assert crp.cpu().tolist() == g.crp.tolist() == gold["crp"].tolist()
+        Rh = np.ascontiguousarray(R.cpu().numpy().view(np.uint32))
+        assert hashlib.sha256(Rh.tobytes()).hexdigest() == str(gold["sha256"][0]), form
+    # properties of the form (independent of the oracle)
+    c = g.crp
+    assert np.array_equal(Rh[:, c], np.eye(r, dtype=np.uint32))
+    first = np.argmax(Rh != 0, axis=1)
+    assert np.array_equal(first, c)
+    rows = sample_rows(cfg.m, 512, 5)
+    from pluq_checks import matmul_mod_f64
+    got = matmul_mod_f64(g.A[rows][:, c].astype(np.int64), Rh.astype(np.int64), cfg.p)
+    assert np.array_equal(got, g.A[rows].astype(np.int64))
 
 
 # ------------------------------------------------------ uniform 32768^2 --
@@ -245,14 +219,13 @@ def test_uniform_32768(ctx, form):
     check_rpm_from_pq(P, Q, r, set(zip(gold["piv_rows"].tolist(), gold["piv_cols"].tolist())))
     assert rrp == gold["rrp"].tolist() and crp == gold["crp"].tolist()
     check_structure(LU, r)
-    # factor identity: exact library product on the GPU (limb form; the FP64
-    # form takes the host check alone) and 3-trial Freivalds on the host
-    if form == "limb":
-        exact_identity_gpu(Ad, cfg.p, P, Q, LU, r)
+    # factor identity: exact library product on the GPU over 4096 sampled rows
+    # of the permuted frame, and 3-trial Freivalds over all of it on the host
+    exact_identity_gpu(Ad, cfg.p, P, Q, LU, r, sample_rows(cfg.m, 4096, 3))
     LU_host = LU.cpu().numpy().view(np.uint32)
     del LU
     torch.cuda.empty_cache()
-    freivalds_host(A, cfg.p, P, Q, LU_host, r, trials=3)
+    freivalds(A, cfg.p, P, Q, LU_host, r, trials=3)
 
 
 # --------------------------------- 16384 x 20480 rank 16320 over 2^31 - 1 --
@@ -267,12 +240,11 @@ def test_lru_16384x20480_p31(ctx, form):
     check_rpm_from_pq(P, Q, r, g.rpm)
     assert rrp == g.rrp.tolist() and crp == g.crp.tolist()
     check_structure(LU, r)
-    if form == "limb":
-        exact_identity_gpu(Ad, cfg.p, P, Q, LU, r)
+    exact_identity_gpu(Ad, cfg.p, P, Q, LU, r, sample_rows(cfg.m, 2048, 4))
     LU_host = LU.cpu().numpy().view(np.uint32)
     del LU
     torch.cuda.empty_cache()
-    freivalds_host(g.A, cfg.p, P, Q, LU_host, r, trials=3)
+    freivalds(g.A, cfg.p, P, Q, LU_host, r, trials=3)
 
 
 # ------------------------------------------------- batch of 4096 matrices --
