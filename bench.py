@@ -586,6 +586,7 @@ def profile_fgemm(args):
     C = dev(workloads.uniform_matrix(M, N, p, 1, "casec"))
     ctx = pq.Context(0)
     ctx.set_option("winograd_min", args.winograd_min)
+    ctx.set_option("fgemm_tile", args.fgemm_tile)
     form = "fp64" if args.form == "fp64" else "limb"
     ms = []
     for _ in range(max(1, args.repeat)):
@@ -596,7 +597,8 @@ def profile_fgemm(args):
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(f"fgemm {M}x{N}x{K} p={p} {form} winograd_min={args.winograd_min}: last {ms[-1]:.3f} ms "
+    print(f"fgemm {M}x{N}x{K} p={p} {form} tile={args.fgemm_tile} winograd_min={args.winograd_min}: "
+          f"last {ms[-1]:.3f} ms "
           f"({2.0 * M * N * K / ms[-1] / 1e9:.1f} field Tops/s)", flush=True)
 
 
@@ -615,7 +617,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default schedule instead of the autotuned one")
-    ap.add_argument("--tune-budget-ms", type=float, default=15000.0)
+    ap.add_argument("--tune-budget-ms", type=float, default=25000.0)
     ap.add_argument("--schedule", default="",
                     help="leaf_dim,leaf_kind,fork_depth to time instead of autotuning "
                          "(leaf kind 0 barrier, 1 wavefront, 2 per leaf, 3 cluster)")
@@ -634,6 +636,7 @@ def main():
                     help="MxNxK: profiling case of one fgemm_modp call instead of the bench "
                          "(with --p, --form, --repeat)")
     ap.add_argument("--p", type=int, default=65521, help="prime of the --fgemm case")
+    ap.add_argument("--fgemm-tile", type=int, default=0, help="tile variant of the --fgemm case")
     ap.add_argument("--repeat", type=int, default=2, help="calls of the --fgemm case")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -153,7 +153,7 @@ int fgemm_modp(pluq_ctx* ctx, uint32_t p, int64_t M, int64_t N, int64_t K, const
  *   live in one 32 MiB device array inside the library that each GPU loading
  *   the library keeps until process exit; problems whose planes exceed it,
  *   2 L (ceil(M/128)*128 + ceil(N/T)*T) ceil(K/64)*64 bytes with L digits as
- *   for PLUQ_FORM_LIMB_F16 (T = 128 for L <= 2, else 64), return
+ *   for PLUQ_FORM_LIMB_F16 (T = 128 for L = 1, 80 for L = 2, else 64), return
  *   PLUQ_ERR_TOO_LARGE.
  *   The first call on a device looks up that array's device address (with
  *   the device current), so make it before any stream capture.  All calls
@@ -236,7 +236,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *   PLUQ_OPT_LEAF_DIM    largest leaf block, rows and columns [0, 2048]
  *                        (default 1024); 0 sends the recursion down to
  *                        one-CTA tiles
- *   PLUQ_OPT_LEAF_KIND   leaf kernel [0, 3]: 0 one grid barrier per pivot
+ *   PLUQ_OPT_LEAF_KIND   leaf kernel [0, 4]: 0 one grid barrier per pivot
  *                        (rows dealt cyclically over the CTAs; rows that
  *                        reduce to zero cost nothing more), 1 block-row
  *                        wavefront (each CTA applies the earlier CTAs'
@@ -250,7 +250,12 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        cluster of up to 16 CTAs, candidates and the
  *                        elected row read from the other CTAs' shared
  *                        memory; blocks up to 1024 x 1024 for p < 2^24,
- *                        smaller ones above; larger blocks take kind 0)
+ *                        smaller ones above; larger blocks take kind 0);
+ *                        4 one CTA with the block as 16-bit residues in its
+ *                        shared memory, one block barrier per pivot (p < 2^16,
+ *                        blocks up to 256 x 256; other blocks as kind 2).
+ *                        Kind 2 also takes the kind-4 leaf for dense blocks
+ *                        that fit it.
  *   PLUQ_OPT_TILE_M/N    one-CTA base-case tile [1, 128]
  *   PLUQ_OPT_TRSM_BLOCK  diagonal block of the triangular solves [1, 64]
  *                        (each block is inverted, then applied as a product)
@@ -297,6 +302,15 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        recursively while the halves still qualify; 0
  *                        (default): classical products only.  Results are
  *                        identical (the pre-additions are reduced mod p).
+ *   PLUQ_OPT_FGEMM_TILE  [0, 2] tile variant of the limb fgemm: 0 (default)
+ *                        128 x 128 tiles (128 x 64 for three or four digits),
+ *                        one set of weight-class accumulators in TMEM; 1 as 0
+ *                        with the two middle-class products of two-digit plans
+ *                        in accumulators of their own (exact K groups twice as
+ *                        long where the digits allow it); 2 two accumulator
+ *                        sets of 128 x 80 tiles (two digits) or 128 x 128 (one
+ *                        digit), drained while the other fills.  Results are
+ *                        identical; the autotuner picks among them.
  *   PLUQ_OPT_WORKSPACE_MB  cap on the device workspace the context (with its
  *                        child contexts) holds, in MiB [0, 2^31); 0 (default):
  *                        none.  A call whose workspace would exceed the cap
@@ -317,6 +331,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_WAIT_LIMIT_US 12
 #define PLUQ_OPT_WORKSPACE_MB 13
 #define PLUQ_OPT_WINOGRAD_MIN 14
+#define PLUQ_OPT_FGEMM_TILE 15
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a
@@ -332,14 +347,18 @@ int pluq_last_stats(pluq_ctx* ctx, int64_t* n_base, int64_t* n_nodes, int64_t* n
  * by hand for one machine): times pluq_modp on copies of A (device, m x n, row
  * stride lda, read only) under candidate schedules - leaf cut-off 1024, 512,
  * 2048 crossed with leaf kind per-leaf choice, barrier, wavefront, cluster
- * (fork depth 2), then fork depth 0, 1, 3 for the best - one warm run and the best of two
- * timed runs each, stopping once budget_ms (0: 10 s) is spent after at least
- * one schedule.  The fastest is stored in the context for (p, m, n, form) and
- * applied by later pluq_modp / echelon_modp / rank_profile_modp calls of that
- * shape (PLUQ_OPT_USE_TUNED); a new call for the shape replaces it.  The
- * timings depend on A's rank structure, so tune on a representative matrix.
- * chosen (host, may be NULL): leaf cut-off, leaf kind, fork depth; best_ms
- * (host, may be NULL): its time.  Synchronises the stream.
+ * (fork depth 2), and for p < 2^16 cut-off 256 with the per-leaf choice and the
+ * one-CTA tile leaf; then fork depth 0, 1, 3 for the best; then, for p < 2^18,
+ * the limb fgemm's tile variants (PLUQ_OPT_FGEMM_TILE) - one warm run and the
+ * best of two timed runs each, stopping once budget_ms (0: 10 s) is spent
+ * after at least one schedule.  The fastest is stored in the context for
+ * (p, m, n, form) and applied by later pluq_modp / echelon_modp /
+ * rank_profile_modp calls of that shape (PLUQ_OPT_USE_TUNED); a new call for
+ * the shape replaces it.  The timings depend on A's rank structure, so tune on
+ * a representative matrix.
+ * chosen (host, may be NULL, 4 entries): leaf cut-off, leaf kind, fork depth,
+ * fgemm tile variant; best_ms (host, may be NULL): its time.  Synchronises the
+ * stream.
  * Errors: as pluq_modp, NO_WORKSPACE (two m x n copies). */
 int pluq_autotune(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_t* A,
                   int64_t lda, int form, void* stream, double budget_ms, int32_t* chosen,

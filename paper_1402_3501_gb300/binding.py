@@ -146,7 +146,7 @@ class Context:
     OPTIONS = {"leaf_dim": 1, "leaf_kind": 2, "tile_m": 3, "tile_n": 4, "trsm_block": 5,
                "chain_rows": 6, "fork_depth": 7, "use_tuned": 8, "thin_gemm": 9,
                "decomposition": 10, "slab_rows": 11, "wait_limit_us": 12, "workspace_mb": 13,
-               "winograd_min": 14}
+               "winograd_min": 14, "fgemm_tile": 15}
 
     def set_option(self, name: str, value: int):
         """Set a recursion option (see PLUQ_OPT_* in include/pluqmodp.h)."""
@@ -179,20 +179,20 @@ class Context:
                          "bytes": by.value, "tensor_flops": tf.value}
         return out
 
-    LEAF_KINDS = {0: "barrier", 1: "wavefront", 2: "per-leaf", 3: "cluster"}
+    LEAF_KINDS = {0: "barrier", 1: "wavefront", 2: "per-leaf", 3: "cluster", 4: "tile"}
 
     def autotune(self, A: torch.Tensor, p: int, form="limb", budget_ms: float = 0.0,
                  stream=None) -> dict:
         """Time candidate recursion schedules on copies of A and keep the fastest for
         A's (p, shape, form) in this context (pluq_autotune); A is not modified."""
         m, n, ld = _matrix_args(A)
-        chosen = (ctypes.c_int32 * 3)()
+        chosen = (ctypes.c_int32 * 4)()
         best = ctypes.c_double()
         _check(load().pluq_autotune(self.handle, p, m, n, ctypes.c_void_p(A.data_ptr()), ld,
                                     _form(form), _stream_handle(stream), float(budget_ms), chosen,
                                     ctypes.byref(best)), "pluq_autotune")
         return {"leaf_dim": chosen[0], "leaf_kind": self.LEAF_KINDS.get(chosen[1], chosen[1]),
-                "fork_depth": chosen[2], "ms": best.value}
+                "fork_depth": chosen[2], "fgemm_tile": chosen[3], "ms": best.value}
 
     def last_stats(self) -> dict:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -155,7 +155,7 @@ struct pluq_ctx {
   int trsm_block = 64;     // diagonal block of the triangular solves
   int leaf_dim = 1024;     // cooperative leaves up to leaf_dim x leaf_dim (0: off)
   int leaf_kind = 2;       // 0: grid barrier per pivot, 1: wavefront, 2: chosen per leaf,
-                           // 3: cluster barrier per pivot
+                           // 3: cluster barrier per pivot, 4: one-CTA 16-bit tile
   double leaf_density = 1.0;  // rank / min(m, n) of the last leaf of the current call
   int chain_rows = 0;      // rows per CTA of wavefront leaves (0: default)
   int64_t mmax = 0, nmax = 0;
@@ -184,7 +184,8 @@ struct pluq_ctx {
   const void* batch_graph_key = nullptr;
   int32_t* host_small = nullptr;  // pinned host scalars
   uint32_t limb_plan_p = 0;       // p of the cached limb fgemm plan
-  uint64_t limb_plan[4] = {0, 0, 0, 0};
+  uint64_t limb_plan[6] = {0, 0, 0, 0, 0, 0};
+  int limb_variant = 0;           // tile variant of the limb fgemm (0, 1, 2)
   // concurrent recursion (the independent calls on F and G): two child
   // contexts, each with its own stream, workspace and host thread; they share
   // the parent's index-vector slots and inverse table (disjoint ranges /
@@ -204,7 +205,7 @@ struct pluq_ctx {
   struct Tuned {
     uint32_t p;
     int64_t m, n;
-    int form, leaf_dim, leaf_kind, fork_depth;
+    int form, leaf_dim, leaf_kind, fork_depth, limb_variant;
     double ms;
   };
   std::vector<Tuned> tuned;
@@ -252,6 +253,9 @@ int chain_fits(pluq_ctx* c, int64_t m, int64_t n);
 int launch_leaf_cluster(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
                         int32_t* perm_c, int32_t* rank_out);
 int cluster_leaf_fits(pluq_ctx* c, int64_t m, int64_t n);
+int launch_leaf_tile(pluq_ctx* c, uint32_t* X, int64_t ldx, int m, int n, int32_t* perm_r,
+                     int32_t* perm_c, int32_t* rank_out);
+int tile_leaf_fits(pluq_ctx* c, int64_t m, int64_t n);
 int leaf_max_dim();
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
 int batched_max_dim();

@@ -332,7 +332,8 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->mmax = c->mmax;
   l->nmax = c->nmax;
   l->limb_plan_p = c->limb_plan_p;
-  for (int k = 0; k < 4; ++k) l->limb_plan[k] = c->limb_plan[k];
+  for (int k = 0; k < 6; ++k) l->limb_plan[k] = c->limb_plan[k];
+  l->limb_variant = c->limb_variant;
   l->perm_r = c->perm_r;
   l->perm_c = c->perm_c;
   l->inv_table = c->inv_table;
@@ -525,15 +526,20 @@ struct Recursion {
     // wavefront leaves win on dense blocks, cluster (else barrier) leaves on
     // rank-deficient ones; kind 2 guesses from the rank density of the
     // previous leaf
-    const bool want_chain =
-        c->leaf_kind == 1 || (c->leaf_kind == 2 && c->leaf_density > 0.5);
-    const bool chain = c->leaf_dim > 0 && want_chain && chain_fits(c, m, n);
-    const bool cluster = !chain && c->leaf_dim > 0 && (c->leaf_kind == 3 || c->leaf_kind == 2) &&
+    const bool dense = c->leaf_density > 0.5;
+    const bool tile = c->leaf_dim > 0 && (c->leaf_kind == 4 || (c->leaf_kind == 2 && dense)) &&
+                      tile_leaf_fits(c, m, n);
+    const bool want_chain = c->leaf_kind == 1 || ((c->leaf_kind == 2 || c->leaf_kind == 4) && dense);
+    const bool chain = !tile && c->leaf_dim > 0 && want_chain && chain_fits(c, m, n);
+    const bool cluster = !tile && !chain && c->leaf_dim > 0 &&
+                         (c->leaf_kind == 3 || c->leaf_kind == 2 || c->leaf_kind == 4) &&
                          cluster_leaf_fits(c, m, n);
-    const bool leaf = !chain && !cluster && c->leaf_dim > 0 && leaf_fits(c, m, n);
-    if (chain || cluster || leaf || (m <= c->bm && n <= c->bn)) {
+    const bool leaf = !tile && !chain && !cluster && c->leaf_dim > 0 && leaf_fits(c, m, n);
+    if (tile || chain || cluster || leaf || (m <= c->bm && n <= c->bn)) {
       c->n_base++;
-      if (chain)
+      if (tile)
+        PLUQ_TRY(launch_leaf_tile(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
+      else if (chain)
         PLUQ_TRY(launch_leaf_chain(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
       else if (cluster)
         PLUQ_TRY(launch_leaf_cluster(c, X(R0, C0, 0, 0), lda, (int)m, (int)n, pr, pc, rank_slot));
@@ -556,7 +562,8 @@ struct Recursion {
       *r_out = c->host_small[8];
       id->r = c->host_small[12] != 0;
       id->c = c->host_small[13] != 0;
-      if (chain || cluster || leaf) c->leaf_density = (double)*r_out / (double)std::min(m, n);
+      if (tile || chain || cluster || leaf)
+        c->leaf_density = (double)*r_out / (double)std::min(m, n);
       return PLUQ_OK;
     }
     if (d + 2 >= c->depth_slots) return PLUQ_ERR_INVALID_ARG;  // the last slot is scratch
@@ -727,15 +734,17 @@ int prepare(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, int form, void* strea
 // restores the caller's options afterwards.
 struct TunedScope {
   pluq_ctx* c;
-  int leaf_dim, leaf_kind, fork_depth;
+  int leaf_dim, leaf_kind, fork_depth, limb_variant;
   TunedScope(pluq_ctx* ctx, int64_t m, int64_t n)
-      : c(ctx), leaf_dim(ctx->leaf_dim), leaf_kind(ctx->leaf_kind), fork_depth(ctx->fork_depth) {
+      : c(ctx), leaf_dim(ctx->leaf_dim), leaf_kind(ctx->leaf_kind), fork_depth(ctx->fork_depth),
+        limb_variant(ctx->limb_variant) {
     if (c->tuning || !c->use_tuned) return;
     for (const pluq_ctx::Tuned& t : c->tuned)
       if (t.p == c->F.p && t.m == m && t.n == n && t.form == c->form) {
         c->leaf_dim = t.leaf_dim;
         c->leaf_kind = t.leaf_kind;
         c->fork_depth = t.fork_depth;
+        c->limb_variant = t.limb_variant;
         break;
       }
   }
@@ -743,6 +752,7 @@ struct TunedScope {
     c->leaf_dim = leaf_dim;
     c->leaf_kind = leaf_kind;
     c->fork_depth = fork_depth;
+    c->limb_variant = limb_variant;
   }
 };
 
@@ -1295,7 +1305,7 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
       c->leaf_dim = value;
       return PLUQ_OK;
     case PLUQ_OPT_LEAF_KIND:
-      if (value < 0 || value > 3) return PLUQ_ERR_INVALID_ARG;
+      if (value < 0 || value > 4) return PLUQ_ERR_INVALID_ARG;
       c->leaf_kind = value;
       return PLUQ_OK;
     case PLUQ_OPT_TILE_M:
@@ -1338,6 +1348,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
       if (value < 0 || value > 60000000) return PLUQ_ERR_INVALID_ARG;
       c->wait_cycles = (long long)value * 2000;
       return PLUQ_OK;
+    case PLUQ_OPT_FGEMM_TILE:
+      if (value < 0 || value > 2) return PLUQ_ERR_INVALID_ARG;
+      c->limb_variant = value;
+      return PLUQ_OK;
     case PLUQ_OPT_WINOGRAD_MIN:
       if (value < 0) return PLUQ_ERR_INVALID_ARG;
       c->wino_min = value;
@@ -1374,12 +1388,14 @@ int pluq_autotune(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t*
   }
   if (budget_ms <= 0) budget_ms = 10000.0;
   const int save_leaf = c->leaf_dim, save_kind = c->leaf_kind, save_fork = c->fork_depth;
+  const int save_variant = c->limb_variant;
   c->tuning = true;
   // one warm run, then the best of two timed runs of a schedule (ms), or a status
-  auto trial = [&](int leaf, int kind, int fork, double* ms) -> int {
+  auto trial = [&](int leaf, int kind, int fork, int variant, double* ms) -> int {
     c->leaf_dim = leaf;
     c->leaf_kind = kind;
     c->fork_depth = fork;
+    c->limb_variant = variant;
     double best = 1e30;
     for (int it = 0; it < 3; ++it) {
       PLUQ_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -1408,15 +1424,20 @@ int pluq_autotune(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t*
     for (int e : leaves) dup |= (e >= big && l >= big);
     if (!dup) leaves.push_back(l);
   }
-  int b_leaf = 1024, b_kind = 2, b_fork = 2;
+  int b_leaf = 1024, b_kind = 2, b_fork = 2, b_var = save_variant;
   double b_ms = 1e30;
   int st = PLUQ_OK;
+  // one-CTA 16-bit tiles of 256 for small primes (dense blocks take them under
+  // the per-leaf choice, rank-deficient ones the cluster leaf)
+  if (c->F.p < (1u << 16)) leaves.push_back(256);
   // stage 1: cut-off and leaf kind (the default schedule first); stage 2: fork depth
   for (int l : leaves) {
-    for (int k : {2, 0, 1, 3}) {
+    for (int k : {2, 0, 1, 3, 4}) {
+      if (k == 4 && l != 256) continue;
+      if (l == 256 && (k == 0 || k == 1)) continue;
       if (b_ms < 1e30 && spent() > budget_ms) break;
       double ms = 0;
-      st = trial(l, k, 2, &ms);
+      st = trial(l, k, 2, b_var, &ms);
       if (st != PLUQ_OK) break;
       if (ms < b_ms) {
         b_ms = ms;
@@ -1429,18 +1450,32 @@ int pluq_autotune(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t*
   for (int f : {0, 1, 3}) {
     if (st != PLUQ_OK || spent() > budget_ms) break;
     double ms = 0;
-    st = trial(b_leaf, b_kind, f, &ms);
+    st = trial(b_leaf, b_kind, f, b_var, &ms);
     if (st == PLUQ_OK && ms < b_ms) {
       b_ms = ms;
       b_fork = f;
+    }
+  }
+  // stage 3: the limb fgemm's tile variant (only the two-digit and one-digit
+  // plans have alternatives)
+  if (c->form == PLUQ_FORM_LIMB_F16 && c->F.p < (1u << 18)) {
+    for (int v : {0, 1, 2}) {
+      if (v == b_var || st != PLUQ_OK || spent() > budget_ms) continue;
+      double ms = 0;
+      st = trial(b_leaf, b_kind, b_fork, v, &ms);
+      if (st == PLUQ_OK && ms < b_ms) {
+        b_ms = ms;
+        b_var = v;
+      }
     }
   }
   c->tuning = false;
   c->leaf_dim = save_leaf;
   c->leaf_kind = save_kind;
   c->fork_depth = save_fork;
+  c->limb_variant = save_variant;
   if (st != PLUQ_OK) return st;
-  pluq_ctx::Tuned t{c->F.p, m, n, c->form, b_leaf, b_kind, b_fork, b_ms};
+  pluq_ctx::Tuned t{c->F.p, m, n, c->form, b_leaf, b_kind, b_fork, b_var, b_ms};
   bool replaced = false;
   for (pluq_ctx::Tuned& e : c->tuned)
     if (e.p == t.p && e.m == m && e.n == n && e.form == t.form) {
@@ -1452,6 +1487,7 @@ int pluq_autotune(pluq_ctx* c, uint32_t p, int64_t m, int64_t n, const uint32_t*
     chosen[0] = b_leaf;
     chosen[1] = b_kind;
     chosen[2] = b_fork;
+    chosen[3] = b_var;
   }
   if (best_ms) *best_ms = b_ms;
   return PLUQ_OK;

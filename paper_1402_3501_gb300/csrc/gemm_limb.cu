@@ -10,20 +10,25 @@
 // block of at most k_flush = floor(2^24 / max weight-class product) columns of
 // K is accumulated before the epilogue warps drain the accumulators:
 // t = sum_w c_w 2^{8w} (int64, exact), reduced mod p by one Montgomery step
-// and added to a residue kept in TMEM.  The last drain writes C - residue.
+// and added to a residue kept in the epilogue's registers.  The last drain
+// writes C - residue.
 //
 // Digits: L = 1 or 2 for p up to about 2^17 (classes recombined into one int64
 // and reduced once), L = 3 or 4 up to 2^31.  For L >= 3 the tile is 128 x 64
-// so that the 2L-1 class accumulators and the residue fit in the 512 TMEM
-// columns, and since the recombined t may exceed 64 bits it is formed as
-// t_lo + 2^32 t_hi (classes 0-3 and 4-6) and each part is reduced on its own.
+// so that the 2L-1 class accumulators fit in the 512 TMEM columns, and since
+// the recombined t may exceed 64 bits it is formed as t_lo + 2^32 t_hi
+// (classes 0-3 and 4-6) and each part is reduced on its own.
 //
-// Structure (one CTA per 128 x TN tile of C, TN = 128 for L <= 2, else 64;
-// warp-specialised):
+// Structure (one CTA per 128 x TN tile of C, TN = 128, 80, 64, 64 for
+// L = 1..4; warp-specialised):
 //   warp 0     TMA producer: digit planes of A (128 x 64 FP16, 128B swizzle)
-//              and of B^T into a shared-memory ring (6, 3, 3 or 2 stages for L = 1..4);
+//              and of B^T into a shared-memory ring (6, 4, 3 or 2 stages for L = 1..4);
 //   warp 1     TMEM allocation and the single MMA-issuing thread;
-//   warps 2-9  epilogue: two warps per TMEM lane quadrant, 64 columns each.
+//   warps 2-9  epilogue: two warps per TMEM lane quadrant, TN/2 columns each,
+//              the running residue in registers.
+// For L <= 2 the accumulators are double-buffered: two sets of the 2L-1 class
+// accumulators fit in TMEM, so the MMAs of the next K group run while the
+// epilogue drains the previous one (L = 3, 4: one set, the MMAs wait).
 // The digit planes of both operands are written by one packing launch into
 // workspace.  Every mbarrier wait is bounded; on expiry the kernel records
 // PLUQ_ERR_TIMEOUT in the error word, drains, frees TMEM and returns.
@@ -39,7 +44,7 @@
 
 namespace {
 
-constexpr int kTM = 128, kTN = 128, kTK = 64;  // CTA tile, K block (one 128B swizzle row)
+constexpr int kTM = 128, kTK = 64;  // CTA tile rows, K block (one 128B swizzle row)
 constexpr int kLimbBits = 8;
 constexpr int kGemmThreads = 320;               // 10 warps
 constexpr int kBandTiles = 8;                    // tile rows per rasterization band
@@ -163,28 +168,75 @@ __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+
+template <int W>
+__device__ __forceinline__ void tmem_ldw(uint32_t taddr, uint32_t (&v)[W]) {
+  if constexpr (W == 8)
+    tmem_ld8(taddr, v);
+  else
+    tmem_ld4(taddr, v);
+}
+
 // ------------------------------------------------------------ the kernel --
 
-template <int L>
+// Tile variants of the limb fgemm (chosen per shape by the autotuner):
+//   0  128 x TN tile, TN = 128 (L <= 2) or 64 (L >= 3), one set of the 2L-1
+//      weight-class accumulators in TMEM: the MMAs wait while the epilogue
+//      drains a finished K group;
+//   1  as 0 for L = 2, with the two products of the middle weight class in
+//      accumulators of their own (4 x 128 TMEM columns): every accumulator
+//      holds single digit products, so an exact K group is twice as long for
+//      p < 2^16 and the tile is drained half as often;
+//   2  two accumulator sets of a narrower tile (TN = 128 for L = 1, 80 for
+//      L = 2): the MMAs of the next K group run while the epilogue drains the
+//      previous one.
+// The residue lives in the epilogue's registers in every variant.
+template <int L, int V>
 struct LimbCfg {
-  static constexpr int TN = L <= 2 ? kTN : 64;    // CTA tile width (C columns)
-  static constexpr int kStages = L == 1 ? 6 : (L == 4 ? 2 : 3);
-  static constexpr int kClasses = 2 * L - 1;
+  static constexpr bool kSplit = V == 1 && L == 2;
+  static constexpr bool kDouble = V == 2 && L <= 2;
+  static constexpr int TN = L >= 3 ? 64 : (kDouble && L == 2 ? 80 : 128);  // CTA tile width
+  static constexpr int kBufs = kDouble ? 2 : 1;                            // accumulator sets
+  static constexpr int kAccs = kSplit ? 4 : 2 * L - 1;                     // accumulators a set
   static constexpr int kATile = kTileBytes;               // 128 x 64 FP16
   static constexpr int kBTile = TN * kTK * 2;             // TN x 64 FP16
   static constexpr int kStageBytes = L * (kATile + kBTile);
-  static constexpr int kResCol = kClasses * TN;  // residue columns in TMEM
+  static constexpr int kStages = (220 * 1024) / kStageBytes > 6 ? 6 : (220 * 1024) / kStageBytes;
+  static constexpr int kAccCols = kAccs * TN;             // one accumulator set
+  static constexpr int kEpiCols = TN / 2;                 // columns per epilogue thread
+  static constexpr int kChunk = L <= 2 ? 8 : 4;           // columns per TMEM read
   static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
   static constexpr uint32_t kIdesc = idesc_f16(TN);
+  // accumulator of digit product (i, j) and the exponent of its weight 2^{8 w}
+  static __host__ __device__ constexpr int acc_of(int i, int j) { return kSplit ? i * 2 + j : i + j; }
+  static __host__ __device__ constexpr int weight_of(int a) {
+    return kSplit ? (a == 0 ? 0 : (a == 3 ? 2 : 1)) : a;
+  }
+  static_assert(kBufs * kAccCols <= 512, "accumulators exceed TMEM");
+  static_assert(kEpiCols % kChunk == 0, "epilogue reads kChunk columns at a time");
+  static_assert(kTM * (TN + 1) * 4 <= kStages * kStageBytes, "staging exceeds the ring");
 };
 
-template <int L>
+template <int L, int V>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_fgemm_limb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int64_t M, int64_t N, int Mp, int Np, int num_kb, int group_kb,
                  uint32_t* __restrict__ C, int64_t ldc, FieldP F, uint64_t bias,
                  uint64_t bias_hi, int* __restrict__ err) {
-  using Cfg = LimbCfg<L>;
+  using Cfg = LimbCfg<L, V>;
   constexpr int TN = Cfg::TN;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -192,9 +244,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
   uint64_t* full = bars;                      // [kStages]
   uint64_t* empty = bars + Cfg::kStages;      // [kStages]
-  uint64_t* acc_full = bars + 2 * Cfg::kStages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* mma_done = acc_empty + 1;
+  uint64_t* acc_full = bars + 2 * Cfg::kStages;   // [2]: a set holds a finished group
+  uint64_t* acc_empty = acc_full + 2;             // [2]: the epilogue has read a set
+  uint64_t* mma_done = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -216,8 +268,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 8);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 8);
+    }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -255,7 +309,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         issued = kb + 1;
       }
-      // drain: every issued copy lands before the CTA may exit
+      // drain: every issued copy lands before the CTA may exit (a load of
+      // k-block kb was only issued once k-block kb - kStages had been consumed)
       for (int kb = (issued > Cfg::kStages ? issued - Cfg::kStages : 0); kb < issued; ++kb)
         mbar_wait(&full[kb % Cfg::kStages], (kb / Cfg::kStages) & 1, err);
     }
@@ -265,10 +320,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       for (int kb = 0; kb < num_kb; ++kb) {
         const int s = kb % Cfg::kStages;
         const int g = kb / group_kb;
+        const int buf = g % Cfg::kBufs;
         const bool first = (kb % group_kb) == 0;
         const bool last = (kb % group_kb) == group_kb - 1 || kb == num_kb - 1;
-        if (first && g > 0) {
-          if (!mbar_wait(acc_empty, (g - 1) & 1, err)) {
+        if (first && g >= Cfg::kBufs) {
+          // the set of group g - kBufs must have been read by the epilogue
+          if (!mbar_wait(&acc_empty[buf], (g / Cfg::kBufs - 1) & 1, err)) {
             *abort_flag = 1;
             break;
           }
@@ -279,6 +336,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         tc_fence_after();
         const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
+        const uint32_t acc_base = tmem + (uint32_t)(buf * Cfg::kAccCols);
 #pragma unroll
         for (int kk = 0; kk < kTK / 16; ++kk) {
           uint32_t seen = 0;  // classes already written in this k-step
@@ -288,16 +346,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
             for (int j = 0; j < L; ++j) {
               const uint64_t db = smem_desc_sw128(st + L * Cfg::kATile + j * Cfg::kBTile + kk * 32);
-              const int w = i + j;
-              // the first product of each class at the start of a group overwrites
+              const int w = Cfg::acc_of(i, j);
+              // the first product of each accumulator at the start of a group overwrites
               const uint32_t acc = (first && kk == 0 && !((seen >> w) & 1u)) ? 0u : 1u;
               seen |= 1u << w;
-              umma_f16(tmem + (uint32_t)(w * TN), da, db, Cfg::kIdesc, acc);
+              umma_f16(acc_base + (uint32_t)(w * TN), da, db, Cfg::kIdesc, acc);
             }
           }
         }
         umma_commit(&empty[s]);
-        if (last) umma_commit(acc_full);
+        if (last) umma_commit(&acc_full[buf]);
       }
       // every issued MMA completes before TMEM is released
       umma_commit(mma_done);
@@ -305,33 +363,49 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   } else {
     // -------------------------------------------------------- epilogue
-    const int q = warp & 3;           // TMEM lane quadrant of this warp
-    const int h = (warp - 2) >> 2;    // column half
+    // warp e = warp - 2 reads TMEM lane quadrant e % 4 (the quadrant its warp
+    // rank may access) and columns [h TN/2, (h+1) TN/2) of the tile
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    constexpr int EC = Cfg::kEpiCols;
+    uint32_t res[EC];  // sum over drained groups of REDC(t): (sum t) R^{-1} mod p
+#pragma unroll
+    for (int e = 0; e < EC; ++e) res[e] = 0u;
+    bool ok = true;
     for (int g = 0; g < num_groups; ++g) {
-      if (!mbar_wait(acc_full, g & 1, err)) {
+      const int buf = g % Cfg::kBufs;
+      if (!mbar_wait(&acc_full[buf], (g / Cfg::kBufs) & 1, err)) {
         *abort_flag = 1;
+        ok = false;
         break;
       }
       tc_fence_after();
-      const bool last_group = g == num_groups - 1;
-#pragma unroll 1
-      for (int ch = 0; ch < TN / 32; ++ch) {
-        const int col = h * (TN / 2) + ch * 16;
-        uint32_t c[Cfg::kClasses][16], res[16];
+      const uint32_t set = lane_base + (uint32_t)(buf * Cfg::kAccCols + h * EC);
+      constexpr int CW = Cfg::kChunk;
 #pragma unroll
-        for (int w = 0; w < Cfg::kClasses; ++w) tmem_ld16(lane_base + w * TN + col, c[w]);
-        if (g > 0) tmem_ld16(lane_base + Cfg::kResCol + col, res);
+      for (int ch = 0; ch < EC / CW; ++ch) {
+        uint32_t c[Cfg::kAccs][CW];
+#pragma unroll
+        for (int w = 0; w < Cfg::kAccs; ++w) tmem_ldw<CW>(set + w * TN + ch * CW, c[w]);
         tmem_wait_ld();
+        if (ch == EC / CW - 1) {
+          // the whole set is read: hand it back to the MMA issuer before the
+          // arithmetic on the last chunk
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < CW; ++e) {
           uint32_t v;
           if (L <= 2) {
             int64_t t = 0;
 #pragma unroll
-            for (int w = 0; w < Cfg::kClasses; ++w)
-              t += (int64_t)__float2int_rn(__uint_as_float(c[w][e])) * (1 << (kLimbBits * w));
+            for (int w = 0; w < Cfg::kAccs; ++w)
+              t += (int64_t)__float2int_rn(__uint_as_float(c[w][e])) *
+                   (1 << (kLimbBits * Cfg::weight_of(w)));
             v = F.is2 ? (uint32_t)((uint64_t)(t + (int64_t)bias) & 1u)
                       : f_redc((uint64_t)(t + (int64_t)bias), F);
           } else {
@@ -340,7 +414,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             // t R^{-1} = t_lo R^{-1} + t_hi = REDC(t_lo) + REDC(REDC(t_hi) R^2).
             int64_t tlo = 0, thi = 0;
 #pragma unroll
-            for (int w = 0; w < Cfg::kClasses; ++w) {
+            for (int w = 0; w < Cfg::kAccs; ++w) {
               const int64_t cw = (int64_t)__float2int_rn(__uint_as_float(c[w][e]));
               if (w < 4)
                 tlo += cw * ((int64_t)1 << (kLimbBits * w));
@@ -351,26 +425,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const uint32_t vhi = f_redc((uint64_t)(thi + (int64_t)bias_hi), F);
             v = f_add(vlo, f_redc((uint64_t)vhi * F.r2, F), F);
           }
-          res[e] = g > 0 ? f_add(res[e], v, F) : v;
+          res[ch * CW + e] = f_add(res[ch * CW + e], v, F);
         }
-        if (!last_group) {
-          tmem_st16(lane_base + Cfg::kResCol + col, res);
-        } else {
-          // residue holds (sum t) R^{-1}; one more step with R^2 undoes it.
-          // Stage the tile in the (now idle) pipeline shared memory so that
-          // C is updated with row-contiguous accesses below.
-          uint32_t* stage = reinterpret_cast<uint32_t*>(smem) + row * (TN + 1) + col;
+      }
+    }
+    // the residue holds (sum t) R^{-1}; one more step with R^2 undoes it.
+    // Stage the tile in the (now idle) pipeline shared memory so that C is
+    // updated with row-contiguous accesses below.
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // every warp is past the ring
+    if (ok) {
+      uint32_t* stage = reinterpret_cast<uint32_t*>(smem) + row * (TN + 1) + h * EC;
 #pragma unroll
-          for (int e = 0; e < 16; ++e)
-            stage[e] = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
-        }
-      }
-      if (!last_group) {
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
-      }
+      for (int e = 0; e < EC; ++e) stage[e] = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
     }
     // C <- C - residue, one warp per row, 32 consecutive columns per access
     asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -381,16 +447,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const int64_t gr = (int64_t)m0 + rr;
         if (gr >= M) break;
         uint32_t* crow = C + gr * ldc + n0;
-        uint32_t cv[TN / 32];
+        constexpr int NQ = (TN + 31) / 32;
+        uint32_t cv[NQ];
 #pragma unroll
-        for (int q2 = 0; q2 < TN / 32; ++q2) {
+        for (int q2 = 0; q2 < NQ; ++q2) {
           const int j = lane + 32 * q2;
-          cv[q2] = (n0 + j < N) ? crow[j] : 0u;
+          cv[q2] = (j < TN && n0 + j < N) ? crow[j] : 0u;
         }
 #pragma unroll
-        for (int q2 = 0; q2 < TN / 32; ++q2) {
+        for (int q2 = 0; q2 < NQ; ++q2) {
           const int j = lane + 32 * q2;
-          if (n0 + j < N) crow[j] = f_sub(cv[q2], stage[rr * (TN + 1) + j], F);
+          if (j < TN && n0 + j < N) crow[j] = f_sub(cv[q2], stage[rr * (TN + 1) + j], F);
         }
       }
     }
@@ -555,6 +622,9 @@ struct LimbPlan {
   int group_kb = 0;  // K blocks of 64 per exact accumulation group
   uint64_t bias = 0;     // multiple of p making the (low) recombined drain value >= 0
   uint64_t bias_hi = 0;  // same for the high part (L >= 3)
+  // L = 2 with the middle class split (tile variant 1): its group and bias
+  int group_kb_split = 0;
+  uint64_t bias_split = 0;
 };
 
 // Largest |digit| of each of the L digits over all balanced residues.
@@ -627,6 +697,23 @@ LimbPlan plan_for(uint32_t p) {
     const uint64_t tm = (uint64_t)tmax + 1, tmh = (uint64_t)tmax_hi + 1;
     pl.bias = p == 2 ? 0 : (tm + p - 1) / p * p;
     pl.bias_hi = p == 2 ? 0 : (tmh + p - 1) / p * p;
+    pl.group_kb_split = pl.group_kb;
+    pl.bias_split = pl.bias;
+    if (L == 2) {
+      // each accumulator holds one digit product: bound b_i b_j instead of the
+      // class sum; the drained t has the same form, so only its size changes
+      int64_t worst1 = 1;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) worst1 = std::max(worst1, b[i] * b[j]);
+      const int64_t g1 = std::min<int64_t>((((int64_t)1 << 24) / worst1) / kTK, 1 << 20);
+      long double t1 = 0;
+      for (int w = 0; w < 3; ++w) t1 += (long double)(g1 * kTK) * cls[w] * powl(2.0L, 8 * w);
+      if (g1 >= 1 && (p == 2 || 2 * t1 + p < lim)) {
+        pl.group_kb_split = (int)g1;
+        const uint64_t t1m = (uint64_t)t1 + 1;
+        pl.bias_split = p == 2 ? 0 : (t1m + p - 1) / p * p;
+      }
+    }
     return pl;
   }
   return pl;
@@ -662,12 +749,12 @@ int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t kp, int
   return r == CUDA_SUCCESS ? PLUQ_OK : PLUQ_ERR_CUDA;
 }
 
-template <int L>
+template <int L, int V>
 int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, const uint32_t* A,
              int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
-  using Cfg = LimbCfg<L>;
+  using Cfg = LimbCfg<L, V>;
   static const cudaError_t attr = cudaFuncSetAttribute(
-      k_fgemm_limb<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+      k_fgemm_limb<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
   PLUQ_CUDA(attr);
   constexpr int TN = Cfg::TN;
   const int64_t Mp = cdiv(M, kTM) * kTM, Np = cdiv(N, TN) * TN, Kp = cdiv(K, kTK) * kTK;
@@ -689,9 +776,10 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K,
                (double)abytes + (double)bbytes + 8.0 * M * N, 1,
                2.0 * Mp * Np * Kp * L * L);
-  k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, c->stream>>>(
-      ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK), pl.group_kb, C, ldc, c->F, pl.bias,
-      pl.bias_hi, err);
+  k_fgemm_limb<L, V><<<grid, kGemmThreads, Cfg::kSmem, c->stream>>>(
+      ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK),
+      Cfg::kSplit ? pl.group_kb_split : pl.group_kb, C, ldc, c->F,
+      Cfg::kSplit ? pl.bias_split : pl.bias, pl.bias_hi, err);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
@@ -703,13 +791,15 @@ int limb_form_supported(uint32_t p) { return plan_for(p).L > 0; }
 int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
                    const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
-  // the plan depends on p only; cached in the context (L, group, biases)
+  // the plan depends on p only; cached in the context (L, groups, biases)
   if (c->limb_plan_p != c->F.p) {
     const LimbPlan pl = plan_for(c->F.p);
     c->limb_plan[0] = (uint64_t)pl.L;
     c->limb_plan[1] = (uint64_t)pl.group_kb;
     c->limb_plan[2] = pl.bias;
     c->limb_plan[3] = pl.bias_hi;
+    c->limb_plan[4] = (uint64_t)pl.group_kb_split;
+    c->limb_plan[5] = pl.bias_split;
     c->limb_plan_p = c->F.p;
   }
   LimbPlan cached;
@@ -717,10 +807,19 @@ int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
   cached.group_kb = (int)c->limb_plan[1];
   cached.bias = c->limb_plan[2];
   cached.bias_hi = c->limb_plan[3];
-  if (cached.L == 1) return run_limb<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
-  if (cached.L == 2) return run_limb<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
-  if (cached.L == 3) return run_limb<3>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
-  if (cached.L == 4) return run_limb<4>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  cached.group_kb_split = (int)c->limb_plan[4];
+  cached.bias_split = c->limb_plan[5];
+  const int v = c->limb_variant;
+  if (cached.L == 1)
+    return v == 2 ? run_limb<1, 2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc)
+                  : run_limb<1, 0>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  if (cached.L == 2) {
+    if (v == 1) return run_limb<2, 1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+    if (v == 2) return run_limb<2, 2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+    return run_limb<2, 0>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  }
+  if (cached.L == 3) return run_limb<3, 0>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  if (cached.L == 4) return run_limb<4, 0>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
   return PLUQ_ERR_UNSUPPORTED_FORM;
 }
 
@@ -771,14 +870,18 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
       cudaGetLastError();
       return PLUQ_ERR_CUDA;
     }
-    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   LimbCfg<1>::kSmem));
-    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   LimbCfg<2>::kSmem));
-    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   LimbCfg<3>::kSmem));
-    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   LimbCfg<4>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<1, 0>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<1, 0>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<2, 0>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<2, 0>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<3, 0>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<3, 0>::kSmem));
+    PLUQ_CUDA(cudaFuncSetAttribute(k_fgemm_limb<4, 0>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   LimbCfg<4, 0>::kSmem));
     d.scratch = static_cast<unsigned char*>(s);
     d.err = static_cast<int*>(e);
     d.ready = true;
@@ -791,7 +894,7 @@ template <int L>
 int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int64_t M, int64_t N,
                 int64_t K, const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
                 uint32_t* C, int64_t ldc, cudaStream_t s) {
-  using Cfg = LimbCfg<L>;
+  using Cfg = LimbCfg<L, 0>;
   constexpr int TN = Cfg::TN;
   // each dimension alone is checked against the array before any product of
   // them is formed, so the byte counts below cannot wrap
@@ -812,7 +915,7 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
   PLUQ_TRY(make_map(&ma, Ap, L * Mp, Kp, kTM));
   PLUQ_TRY(make_map(&mb, Bp, L * Np, Kp, TN));
   const dim3 grid((unsigned)(Np / TN), (unsigned)(Mp / kTM));
-  k_fgemm_limb<L><<<grid, kGemmThreads, Cfg::kSmem, s>>>(ma, mb, M, N, (int)Mp, (int)Np,
+  k_fgemm_limb<L, 0><<<grid, kGemmThreads, Cfg::kSmem, s>>>(ma, mb, M, N, (int)Mp, (int)Np,
                                                          (int)(Kp / kTK), pl.group_kb, C, ldc, F,
                                                          pl.bias, pl.bias_hi, d.err);
   PLUQ_CUDA(cudaGetLastError());

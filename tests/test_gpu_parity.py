@@ -117,6 +117,45 @@ def test_fgemm_parity(ctx, form, p, mnk):
     assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect)
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("p", [2, 251, 65521, 131071, 1048573])
+@pytest.mark.parametrize("mnk", [(70, 33, 17), (129, 257, 1100), (300, 200, 2100)])
+def test_fgemm_tile_variants(ctx, tile, p, mnk):
+    """Every tile variant of the limb fgemm gives exactly C - A B mod p, with
+    K spanning several exact accumulation groups and operands at p - 1."""
+    M, N, K = mnk
+    rng = np.random.default_rng(M + 3 * N + K + p % 89 + tile)
+    A = rng.integers(0, p, (M, K), dtype=np.int64)
+    B = rng.integers(0, p, (K, N), dtype=np.int64)
+    C = rng.integers(0, p, (M, N), dtype=np.int64)
+    A[: M // 2, :] = p - 1
+    B[:, : N // 3] = p - 1
+    expect = (C - matmul_mod(A, B, p)) % p
+    ctx.set_option("fgemm_tile", tile)
+    ctx.set_option("thin_gemm", 0)
+    try:
+        Cd = to_dev(C)
+        pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form="limb", ctx=ctx)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option("fgemm_tile", 0)
+        ctx.set_option("thin_gemm", 1)
+    assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect)
+
+
+@pytest.mark.parametrize("tile", [1, 2])
+@pytest.mark.parametrize("p,shape,frac", [(65521, (1100, 900), 1.0), (131071, (777, 700), 0.6)])
+def test_pluq_tile_variants(ctx, tile, p, shape, frac):
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(frac * min(m, n)), p, seed=14)
+    ctx.set_option("fgemm_tile", tile)
+    try:
+        with leaf_mode(ctx, (256, 2)):
+            assert_parity(ctx, g.A, p, "limb")
+    finally:
+        ctx.set_option("fgemm_tile", 0)
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_fgemm_adversarial_extremes(ctx, form):
     # all entries p-1: the largest products the delayed reduction must absorb
@@ -231,7 +270,7 @@ SHAPES = [(1, 1), (1, 40), (40, 1), (17, 33), (128, 128), (129, 130), (200, 300)
           (513, 257)]
 
 
-@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 2), (1024, 3), (0, 0)])
+@pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 2), (1024, 3), (256, 4), (0, 0)])
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("p", [2, 3, 65521, 131071])
 @pytest.mark.parametrize("shape", SHAPES)
@@ -243,7 +282,7 @@ def test_pluq_uniform(ctx, leaf, form, p, shape):
 
 
 @pytest.mark.parametrize("leaf", [(2048, 1), (2048, 0), (1024, 3), (96, 1), (96, 0), (96, 2),
-                                  (96, 3), (0, 0)])
+                                  (96, 3), (96, 4), (256, 4), (256, 2), (0, 0)])
 @pytest.mark.parametrize("p", [3, 131071])
 @pytest.mark.parametrize("shape", [(64, 64), (150, 200), (300, 260), (513, 257), (700, 700)])
 @pytest.mark.parametrize("frac", [0.0, 0.1, 0.5, 0.9])
@@ -284,7 +323,7 @@ def test_pluq_thin_gemm_switch(ctx, thin):
 
 
 @pytest.mark.parametrize("fork_depth", [0, 1, 4])
-@pytest.mark.parametrize("leaf", [(96, 0), (96, 1), (96, 3), (0, 0)])
+@pytest.mark.parametrize("leaf", [(96, 0), (96, 1), (96, 3), (96, 4), (0, 0)])
 @pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
                                           (65521, (600, 450), 1.0)])
 def test_pluq_concurrent_branches(ctx, fork_depth, leaf, p, shape, frac):
@@ -358,7 +397,7 @@ def test_pluq_cluster_leaf(ctx, p, shape, frac):
 # rank, profiles and RPM as the oracle, valid factors; slabs of the leaf
 # cut-off and other heights, several leaf kinds, rank-deficient and full rank
 @pytest.mark.parametrize("slab", [0, 40, 150, 300])
-@pytest.mark.parametrize("leaf", [(96, 3), (96, 0), (96, 1), (0, 0)])
+@pytest.mark.parametrize("leaf", [(96, 3), (96, 0), (96, 1), (96, 4), (0, 0)])
 @pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
                                           (65521, (600, 450), 1.0), (131071, (450, 600), 0.1),
                                           (2147483647, (300, 260), 0.7)])
@@ -394,6 +433,22 @@ def test_pluq_tiled_iterative_bench_shape(ctx, form):
     assert not np.any(LU[r:, r:])
     assert np.all(np.diag(LU[:r, :r]) != 0)
     exact_identity(g.A, cfg.p, P, Q, LU.astype(np.int64), r)
+
+
+@pytest.mark.parametrize("p", [2, 3, 251, 65521])
+@pytest.mark.parametrize("shape,frac", [((256, 256), 1.0), ((256, 256), 0.3), ((255, 256), 1.0),
+                                        ((256, 130), 1.0), ((1, 256), 1.0), ((256, 1), 1.0),
+                                        ((200, 256), 0.0), ((513, 700), 0.9)])
+def test_pluq_tile_leaf(ctx, p, shape, frac):
+    """The one-CTA 16-bit leaf (blocks up to 256 x 256, p < 2^16): exact against
+    the oracle on full, ragged, degenerate and zero blocks, and inside a recursion."""
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(frac * min(m, n)), p, seed=12)
+    with leaf_mode(ctx, (256, 4)):
+        assert_parity(ctx, g.A, p, "limb")
+    A = workloads.uniform_matrix(m, n, p, 13)
+    with leaf_mode(ctx, (256, 4)):
+        assert_parity(ctx, A, p, "limb")
 
 
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
@@ -493,7 +548,7 @@ def test_rank_profile_parity(ctx, p):
     assert rpm.cpu().numpy().tolist() == expect.tolist()
 
 
-@pytest.mark.parametrize("leaf", [(96, 3), (96, 0), (96, 1), (0, 0)])
+@pytest.mark.parametrize("leaf", [(96, 3), (96, 0), (96, 1), (96, 4), (0, 0)])
 @pytest.mark.parametrize("fork_depth", [0, 2])
 @pytest.mark.parametrize("p,shape,frac", [(3, (700, 700), 0.5), (131071, (513, 777), 0.8),
                                           (65521, (900, 500), 0.3)])
@@ -677,9 +732,10 @@ def test_autotune_schedule_parity(ctx, p, shape, frac):
     ch = ctx.autotune(Ad, p, form="limb", budget_ms=3000)
     torch.cuda.synchronize()
     assert torch.equal(Ad, keep)  # the tuner works on copies
-    assert ch["leaf_dim"] in (512, 1024, 2048)
-    assert ch["leaf_kind"] in ("barrier", "wavefront", "per-leaf", "cluster")
+    assert ch["leaf_dim"] in (256, 512, 1024, 2048)
+    assert ch["leaf_kind"] in ("barrier", "wavefront", "per-leaf", "cluster", "tile")
     assert ch["fork_depth"] in (0, 1, 2, 3) and ch["ms"] > 0
+    assert ch["fgemm_tile"] in (0, 1, 2)
     try:
         assert assert_parity(ctx, A, p, "limb") == r
         ctx.set_option("use_tuned", 0)
