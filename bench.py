@@ -386,6 +386,7 @@ def bench_ours(args, world, rank, local):
     schedule = None
     if args.winograd_min:
         ctx.set_option("winograd_min", args.winograd_min)
+    ctx.set_option("fgemm_tile", args.fgemm_tile)
     if args.decomposition == "iterative":
         ctx.set_option("decomposition", 1)
         ctx.set_option("slab_rows", args.slab_rows)
@@ -395,7 +396,7 @@ def bench_ours(args, world, rank, local):
         ctx.set_option("leaf_kind", kind)
         ctx.set_option("fork_depth", fork)
         schedule = {"leaf_dim": leaf, "leaf_kind": ctx.LEAF_KINDS[kind], "fork_depth": fork,
-                    "set": "by --schedule"}
+                    "fgemm_tile": args.fgemm_tile, "set": "by --schedule"}
     elif not args.no_autotune:
         schedule = ctx.autotune(A0, p, form=form, budget_ms=args.tune_budget_ms)
     for _ in range(args.warmup):
@@ -636,7 +637,9 @@ def main():
                     help="MxNxK: profiling case of one fgemm_modp call instead of the bench "
                          "(with --p, --form, --repeat)")
     ap.add_argument("--p", type=int, default=65521, help="prime of the --fgemm case")
-    ap.add_argument("--fgemm-tile", type=int, default=0, help="tile variant of the --fgemm case")
+    ap.add_argument("--fgemm-tile", type=int, default=0,
+                    help="limb fgemm tile variant (0-2) of the --fgemm case, and of the bench "
+                         "with --schedule (the autotuner picks it otherwise)")
     ap.add_argument("--repeat", type=int, default=2, help="calls of the --fgemm case")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
