@@ -311,6 +311,12 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        sets of 128 x 80 tiles (two digits) or 128 x 128 (one
  *                        digit), drained while the other fills.  Results are
  *                        identical; the autotuner picks among them.
+ *   PLUQ_OPT_TRSM_STRIP  0, 256 or 512 (default): triangular solves finish a
+ *                        triangle of up to this many rows in one launch (each
+ *                        CTA runs the block substitution over its own strip of
+ *                        32 columns or rows of the right-hand side); 0 keeps
+ *                        one launch per 64-block and per update between them.
+ *                        Takes effect with PLUQ_OPT_TRSM_BLOCK 64.
  *   PLUQ_OPT_WORKSPACE_MB  cap on the device workspace the context (with its
  *                        child contexts) holds, in MiB [0, 2^31); 0 (default):
  *                        none.  A call whose workspace would exceed the cap
@@ -332,6 +338,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_WORKSPACE_MB 13
 #define PLUQ_OPT_WINOGRAD_MIN 14
 #define PLUQ_OPT_FGEMM_TILE 15
+#define PLUQ_OPT_TRSM_STRIP 16
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

@@ -153,6 +153,7 @@ struct pluq_ctx {
   int form = PLUQ_FORM_FP64;
   int bm = 128, bn = 128;  // base-case tile
   int trsm_block = 64;     // diagonal block of the triangular solves
+  int strip_max = 512;     // largest triangle solved by one strip launch (0: none)
   int leaf_dim = 1024;     // cooperative leaves up to leaf_dim x leaf_dim (0: off)
   int leaf_kind = 2;       // 0: grid barrier per pivot, 1: wavefront, 2: chosen per leaf,
                            // 3: cluster barrier per pivot, 4: one-CTA 16-bit tile
@@ -289,6 +290,13 @@ int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uin
                      int64_t ldb, int64_t nrows);
 int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
                     int64_t ldb, int64_t ncols);
+// one-launch solves of a triangle of at most strip_rows(c, count) rows (its
+// 64-blocks inverted beforehand, o the triangle's offset in those blocks)
+int strip_rows(const pluq_ctx* c, int64_t count);
+int trsm_llu_strip(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t o, int64_t r,
+                   uint32_t* B, int64_t ldb, int64_t ncols);
+int trsm_ru_strip(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t o, int64_t r, uint32_t* B,
+                  int64_t ldb, int64_t nrows);
 // C <- C - A B (mod p); A M x K, B K x N, C M x N, all row-major uint32.
 int fgemm_sub(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t* A, int64_t lda,
               const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc);

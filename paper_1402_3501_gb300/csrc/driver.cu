@@ -320,6 +320,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->bm = c->bm;
   l->bn = c->bn;
   l->trsm_block = c->trsm_block;
+  l->strip_max = c->strip_max;
   l->leaf_dim = c->leaf_dim;
   l->leaf_kind = c->leaf_kind;
   l->leaf_density = c->leaf_density;
@@ -1347,6 +1348,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_WAIT_LIMIT_US:
       if (value < 0 || value > 60000000) return PLUQ_ERR_INVALID_ARG;
       c->wait_cycles = (long long)value * 2000;
+      return PLUQ_OK;
+    case PLUQ_OPT_TRSM_STRIP:
+      if (value != 0 && value != 256 && value != 512) return PLUQ_ERR_INVALID_ARG;
+      c->strip_max = value;
       return PLUQ_OK;
     case PLUQ_OPT_FGEMM_TILE:
       if (value < 0 || value > 2) return PLUQ_ERR_INVALID_ARG;

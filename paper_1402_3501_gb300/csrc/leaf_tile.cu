@@ -9,9 +9,11 @@
 // step every warp reports its first owned row (below the pivot) with a
 // non-zero outside the pivot columns, and the minimum over the 32 reports is
 // the next pivot row, so rows that reduce to zero cost nothing more and one
-// block barrier is taken per pivot.  Lane l of every warp owns the eight
-// columns [8 l, 8 l + 8) of each row (one 16-byte shared-memory word); a lane
-// whose columns are all pivot columns skips the row update.
+// block barrier is taken per pivot.  A row is updated in chunks of eight
+// columns (one 16-byte shared-memory word); a warp spreads the (row, chunk)
+// pairs of its rows below the pivot over its lanes, taking only the chunks
+// from the first one that still holds a non-pivot column, so the work of a
+// step follows the live part of the Schur complement.
 //
 // Products c x mod p (c, x < 2^16, so c x < 2^32) are reduced by Barrett's
 // method with mu = floor(2^32 / p): q = floor(c x mu / 2^32) undershoots the
@@ -101,15 +103,19 @@ __global__ void __launch_bounds__(kTileThreads, 1)
   }
   __syncthreads();
 
-  uint32_t pivmask = 0;  // bit q: column c0 + q is a pivot column
+  // lane c holds the pivot-column mask of chunk c (columns [8c, 8c + 8));
+  // chunks past the last column count as fully eliminated
+  const int nchunk = (n + 7) / 8;
+  uint32_t pivmask = lane < nchunk ? 0u : 0xFFu;
   int r = 0, buf = 0;
   while (true) {
     // elected row: the smallest report
     int istar = cand[buf * kTileWarps + lane];
     for (int o = 16; o > 0; o >>= 1) istar = min(istar, __shfl_xor_sync(full, istar, o));
     if (istar == INT_MAX) break;
+    const uint16_t* Ti = T + istar * kTileMax;
     uint32_t pv[8];
-    unpack8(*reinterpret_cast<const uint4*>(T + istar * kTileMax + c0), pv);
+    unpack8(*reinterpret_cast<const uint4*>(Ti + c0), pv);
     // pivot column: first non-zero of the row outside the pivot columns
     int local = 8;
 #pragma unroll
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
       if (pv[q] != 0u && !((pivmask >> q) & 1u)) local = q;
     const unsigned bal = __ballot_sync(full, local < 8);
     const int src = __ffs(bal) - 1;
-    const int jl = __shfl_sync(full, local, src);  // the pivot's slot in lane src
+    const int jl = __shfl_sync(full, local, src);  // the pivot's slot in chunk src
     const int j0 = 8 * src + jl;
     uint32_t mine = 0;
 #pragma unroll
@@ -131,45 +137,55 @@ __global__ void __launch_bounds__(kTileThreads, 1)
       prow[r] = istar;
       pcol[r] = j0;
     }
-    // eliminate the owned rows below the pivot row
-    const bool active = pivmask != 0xFFu;  // some column of the lane still live
-    int first = INT_MAX;
-    for (int k = 0; k < kTileRowsPerWarp; ++k) {
-      const int l = warp + k * kTileWarps;
-      if (l >= m) break;
-      if (l <= istar) continue;
-      uint16_t* Tl = T + l * kTileMax;
-      const uint32_t wl = Tl[j0];
-      __syncwarp();  // every lane has read the pivot-column entry before it is overwritten
-      bool nz = false;
-      if (wl != 0u) {
-        const uint32_t cm = B.mul(wl, inv);  // multiplier: L entry of row l
-        if (active) {
-          uint32_t x[8];
-          unpack8(*reinterpret_cast<const uint4*>(Tl + c0), x);
+    // live chunks [lo, nchunk): before lo every column is a pivot column
+    const unsigned live = __ballot_sync(full, pivmask != 0xFFu);
+    const int lo = live ? __ffs(live) - 1 : nchunk;
+    const int nlive = nchunk - lo;
+    // this warp's rows below the pivot row: l_k = warp + 32 (kb + k), k < nr;
+    // lane k computes row k's multiplier (its L entry)
+    const int kb = istar < warp ? 0 : (istar - warp) / kTileWarps + 1;
+    const int nr = max(0, min(kTileRowsPerWarp, (m - warp + kTileWarps - 1) / kTileWarps) - kb);
+    uint32_t cm_mine = 0;
+    if (lane < nr) cm_mine = B.mul(T[(warp + kTileWarps * (kb + lane)) * kTileMax + j0], inv);
+    __syncwarp();  // every multiplier is read before chunk src is rewritten
+    // (row, chunk) items of this warp over the live chunks only
+    uint32_t rownz = 0;  // bit k: row k keeps a non-zero outside the pivot columns
+    const int items = nr * nlive;
+    for (int t0 = 0; t0 < items; t0 += 32) {
+      const int t = t0 + lane;
+      const int k = t < items ? t / nlive : 0;
+      const int ch = t < items ? lo + (t - k * nlive) : 0;
+      const uint32_t cm = __shfl_sync(full, cm_mine, k);
+      const uint32_t mask = __shfl_sync(full, pivmask, ch);
+      if (t < items) {
+        uint16_t* Tl = T + (warp + kTileWarps * (kb + k)) * kTileMax + 8 * ch;
+        uint32_t x[8];
+        unpack8(*reinterpret_cast<const uint4*>(Tl), x);
+        bool nz = false;
+        if (cm != 0u) {
+          uint32_t y[8];
+          unpack8(*reinterpret_cast<const uint4*>(Ti + 8 * ch), y);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            if ((pivmask >> q) & 1u) continue;  // L entries and the new pivot column
-            x[q] = B.sub(x[q], B.mul(cm, pv[q]));
+            if ((mask >> q) & 1u) continue;  // L entries and the new pivot column
+            x[q] = B.sub(x[q], B.mul(cm, y[q]));
             nz |= x[q] != 0u;
           }
-          if (lane == src) {
+          if (ch == src) {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
               if (q == jl) x[q] = cm;
           }
-          *reinterpret_cast<uint4*>(Tl + c0) = pack8(x);
-        } else if (lane == src) {
-          Tl[j0] = (uint16_t)cm;
-        }
-      } else if (active) {
-        uint32_t x[8];
-        unpack8(*reinterpret_cast<const uint4*>(Tl + c0), x);
+          *reinterpret_cast<uint4*>(Tl) = pack8(x);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) nz |= !((pivmask >> q) & 1u) && x[q] != 0u;
+          for (int q = 0; q < 8; ++q) nz |= !((mask >> q) & 1u) && x[q] != 0u;
+        }
+        if (nz) rownz |= 1u << k;
       }
-      if (first == INT_MAX && __any_sync(full, nz)) first = l;
     }
+    rownz = __reduce_or_sync(full, rownz);
+    const int first = rownz ? warp + kTileWarps * (kb + __ffs(rownz) - 1) : INT_MAX;
     if (lane == 0) cand[(buf ^ 1) * kTileWarps + warp] = first;
     __syncthreads();
     buf ^= 1;

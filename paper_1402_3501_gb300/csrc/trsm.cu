@@ -270,6 +270,7 @@ int64_t split_point(int64_t r, int64_t tb) {
 int llu_rec(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t o, int64_t r, uint32_t* B,
             int64_t ldb, int64_t ncols) {
   const int64_t tb = c->trsm_block;
+  if (r > tb && r <= strip_rows(c, ncols)) return trsm_llu_strip(c, L, ldl, o, r, B, ldb, ncols);
   if (r <= tb) return apply_diag_block(c, kLowerUnitLeft, o / tb, r, B, ldb, ncols);
   const int64_t r1 = split_point(r, tb);
   PLUQ_TRY(llu_rec(c, L, ldl, o, r1, B, ldb, ncols));
@@ -280,6 +281,7 @@ int llu_rec(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t o, int64_t r, u
 int ru_rec(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t o, int64_t r, uint32_t* B,
            int64_t ldb, int64_t nrows) {
   const int64_t tb = c->trsm_block;
+  if (r > tb && r <= strip_rows(c, nrows)) return trsm_ru_strip(c, U, ldu, o, r, B, ldb, nrows);
   if (r <= tb) return apply_diag_block(c, kUpperRight, o / tb, r, B, ldb, nrows);
   const int64_t r1 = split_point(r, tb);
   PLUQ_TRY(ru_rec(c, U, ldu, o, r1, B, ldb, nrows));
@@ -319,4 +321,218 @@ int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint
   if (r <= 0 || ncols <= 0) return PLUQ_OK;
   PLUQ_TRY(invert_diag_blocks(c, kUpperLeft, U, ldu, r));
   return lu_rec(c, U, ldu, 0, r, B, ldb, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Strip solves: a whole triangle of up to NB diagonal blocks (NB * 64 rows)
+// in one launch.  Columns of B (left solves) or rows of B (right solves) are
+// independent, so each CTA takes a strip of 32 of them into shared memory and
+// runs the block forward substitution on it alone: X_k = T_kk^{-1} B_k with the
+// inverted diagonal block, then B_j -= T_jk X_k for the later blocks j.  The
+// 64 x 64 operand of each product is staged in shared memory in Montgomery
+// form; a 64-term dot product of a Montgomery value and a plain residue is
+// summed exactly in 64 bits and reduced by one REDC (p < 2^26), else one REDC
+// per product.  One launch replaces the 2 NB - 1 launches (diagonal products
+// and the thin updates between them) of the block recursion below NB * 64.
+namespace {
+
+constexpr int kStripW = 32;        // columns (left) or rows (right) per CTA
+constexpr int kStripThreads = 256;
+
+template <bool kBig>
+__device__ __forceinline__ uint32_t dot64(const uint32_t* a, int sa, const uint32_t* x, int sx,
+                                          int len, const FieldP& F) {
+  return mont_dot<kBig>(a, sa, x, sx, len, F);
+}
+
+// Left solve X = L^{-1} B with L unit lower (r x r, r <= NB * 64): CTA owns
+// columns [c0, c0 + 32) of B.
+template <int NB, bool kBig>
+__global__ void __launch_bounds__(kStripThreads)
+    k_trsm_llu_strip(const uint32_t* __restrict__ L, int64_t ldl, int r,
+                     const uint32_t* __restrict__ tinv, uint32_t* __restrict__ B, int64_t ldb,
+                     int64_t ncols, FieldP F) {
+  extern __shared__ uint32_t strip_smem[];
+  uint32_t* Xs = strip_smem;                          // [NB * 64][kStripW + 1]
+  uint32_t* Ws = Xs + NB * kTB * (kStripW + 1);       // [64][65]
+  constexpr int XS = kStripW + 1, WS = kTB + 1;
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * kStripW;
+  const int w = (int)(ncols - c0 < kStripW ? ncols - c0 : kStripW);
+  for (int idx = tid; idx < r * kStripW; idx += kStripThreads) {
+    const int i = idx / kStripW, j = idx % kStripW;
+    Xs[i * XS + j] = j < w ? B[(int64_t)i * ldb + c0 + j] : 0u;
+  }
+  const int nb = (r + kTB - 1) / kTB;
+  const int col = tid % kStripW, rb = tid / kStripW;  // outputs rows rb + 8 q
+  for (int k = 0; k < nb; ++k) {
+    const int sk = min(kTB, r - k * kTB);
+    for (int j = k; j < nb; ++j) {
+      const int sj = min(kTB, r - j * kTB);
+      __syncthreads();  // the previous product's writes to Xs and reads of Ws are done
+      // Ws = T_jk in Montgomery form: the inverted diagonal block for j = k
+      // (already Montgomery), else the block of L
+      if (j == k) {
+        for (int idx = tid; idx < kTB * kTB; idx += kStripThreads)
+          Ws[(idx / kTB) * WS + idx % kTB] = tinv[(size_t)k * kTB * kTB + idx];
+      } else {
+        for (int idx = tid; idx < sj * sk; idx += kStripThreads) {
+          const int i = idx / sk, q = idx % sk;
+          Ws[i * WS + q] = f_to_mont(L[(int64_t)(j * kTB + i) * ldl + k * kTB + q], F);
+        }
+      }
+      __syncthreads();
+      uint32_t res[kTB / 8];
+#pragma unroll
+      for (int t = 0; t < kTB / 8; ++t) {
+        const int i = rb + 8 * t;
+        res[t] = i < sj ? dot64<kBig>(&Ws[i * WS], 1, &Xs[(k * kTB) * XS + col], XS, sk, F) : 0u;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < kTB / 8; ++t) {
+        const int i = rb + 8 * t;
+        if (i >= sj) continue;
+        uint32_t* xp = &Xs[(j * kTB + i) * XS + col];
+        *xp = j == k ? res[t] : f_sub(*xp, res[t], F);
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < r * kStripW; idx += kStripThreads) {
+    const int i = idx / kStripW, j = idx % kStripW;
+    if (j < w) B[(int64_t)i * ldb + c0 + j] = Xs[i * XS + j];
+  }
+}
+
+// Right solve X = B U^{-1} with U upper (r x r, r <= NB * 64): CTA owns rows
+// [t0, t0 + 32) of B; X_k = B_k Uinv_k, then B_j -= X_k U_kj for j > k.
+template <int NB, bool kBig>
+__global__ void __launch_bounds__(kStripThreads)
+    k_trsm_ru_strip(const uint32_t* __restrict__ U, int64_t ldu, int r,
+                    const uint32_t* __restrict__ tinv, uint32_t* __restrict__ B, int64_t ldb,
+                    int64_t nrows, FieldP F) {
+  extern __shared__ uint32_t strip_smem[];
+  constexpr int XS = NB * kTB + 1, WS = kTB + 1;
+  uint32_t* Xs = strip_smem;                  // [32][NB * 64 + 1]
+  uint32_t* Ws = Xs + kStripW * XS;           // [64][65]: Ws[q][c] = T[q][c] (Montgomery)
+  const int tid = threadIdx.x;
+  const int64_t t0 = (int64_t)blockIdx.x * kStripW;
+  const int h = (int)(nrows - t0 < kStripW ? nrows - t0 : kStripW);
+  for (int idx = tid; idx < kStripW * r; idx += kStripThreads) {
+    const int i = idx / r, q = idx % r;
+    Xs[i * XS + q] = i < h ? B[(t0 + i) * ldb + q] : 0u;
+  }
+  const int nb = (r + kTB - 1) / kTB;
+  const int c = tid % kTB, rb = tid / kTB;  // output column c, rows rb + 4 q
+  for (int k = 0; k < nb; ++k) {
+    const int sk = min(kTB, r - k * kTB);
+    for (int j = k; j < nb; ++j) {
+      const int sj = min(kTB, r - j * kTB);
+      __syncthreads();
+      if (j == k) {
+        for (int idx = tid; idx < kTB * kTB; idx += kStripThreads)
+          Ws[(idx / kTB) * WS + idx % kTB] = tinv[(size_t)k * kTB * kTB + idx];
+      } else {
+        for (int idx = tid; idx < sk * sj; idx += kStripThreads) {
+          const int q = idx / sj, cc = idx % sj;
+          Ws[q * WS + cc] = f_to_mont(U[(int64_t)(k * kTB + q) * ldu + j * kTB + cc], F);
+        }
+      }
+      __syncthreads();
+      uint32_t res[kStripW / 4];
+#pragma unroll
+      for (int t = 0; t < kStripW / 4; ++t) {
+        const int i = rb + 4 * t;
+        res[t] = c < sj ? dot64<kBig>(&Ws[c], WS, &Xs[i * XS + k * kTB], 1, sk, F) : 0u;
+      }
+      __syncthreads();
+      if (c < sj) {
+#pragma unroll
+        for (int t = 0; t < kStripW / 4; ++t) {
+          uint32_t* xp = &Xs[(rb + 4 * t) * XS + j * kTB + c];
+          *xp = j == k ? res[t] : f_sub(*xp, res[t], F);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kStripW * r; idx += kStripThreads) {
+    const int i = idx / r, q = idx % r;
+    if (i < h) B[(t0 + i) * ldb + q] = Xs[i * XS + q];
+  }
+}
+
+template <int NB>
+size_t strip_smem_llu() { return sizeof(uint32_t) * (NB * kTB * (kStripW + 1) + kTB * (kTB + 1)); }
+template <int NB>
+size_t strip_smem_ru() { return sizeof(uint32_t) * (kStripW * (NB * kTB + 1) + kTB * (kTB + 1)); }
+
+template <int NB>
+int launch_llu_strip(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r,
+                     const uint32_t* tinv, uint32_t* B, int64_t ldb, int64_t ncols) {
+  const size_t smem = strip_smem_llu<NB>();
+  static const cudaError_t a0 = cudaFuncSetAttribute(
+      k_trsm_llu_strip<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const cudaError_t a1 = cudaFuncSetAttribute(
+      k_trsm_llu_strip<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  PLUQ_CUDA(a0);
+  PLUQ_CUDA(a1);
+  const unsigned g = (unsigned)cdiv(ncols, kStripW);
+  ProfScope ps(c, PC_TRSM, (double)r * r * ncols, 8.0 * r * ncols);
+  if (c->F.p >= (1u << 26))
+    k_trsm_llu_strip<NB, true><<<g, kStripThreads, smem, c->stream>>>(L, ldl, (int)r, tinv, B, ldb,
+                                                                      ncols, c->F);
+  else
+    k_trsm_llu_strip<NB, false><<<g, kStripThreads, smem, c->stream>>>(L, ldl, (int)r, tinv, B,
+                                                                       ldb, ncols, c->F);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+template <int NB>
+int launch_ru_strip(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, const uint32_t* tinv,
+                    uint32_t* B, int64_t ldb, int64_t nrows) {
+  const size_t smem = strip_smem_ru<NB>();
+  static const cudaError_t a0 = cudaFuncSetAttribute(
+      k_trsm_ru_strip<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const cudaError_t a1 = cudaFuncSetAttribute(
+      k_trsm_ru_strip<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  PLUQ_CUDA(a0);
+  PLUQ_CUDA(a1);
+  const unsigned g = (unsigned)cdiv(nrows, kStripW);
+  ProfScope ps(c, PC_TRSM, (double)r * r * nrows, 8.0 * r * nrows);
+  if (c->F.p >= (1u << 26))
+    k_trsm_ru_strip<NB, true><<<g, kStripThreads, smem, c->stream>>>(U, ldu, (int)r, tinv, B, ldb,
+                                                                     nrows, c->F);
+  else
+    k_trsm_ru_strip<NB, false><<<g, kStripThreads, smem, c->stream>>>(U, ldu, (int)r, tinv, B,
+                                                                      ldb, nrows, c->F);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
+}  // namespace
+
+// Largest triangle a strip launch takes for `count` right-hand sides: more
+// diagonal blocks while there are few strips (the launch is latency-bound), fewer
+// when the CUDA-core work of the triangle's blocks would dominate.
+int strip_rows(const pluq_ctx* c, int64_t count) {
+  if (c->trsm_block != kTB || c->strip_max <= 0) return 0;
+  const int rows = count <= 4096 ? 8 * kTB : 4 * kTB;
+  return rows < c->strip_max ? rows : c->strip_max;
+}
+
+int trsm_llu_strip(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t o, int64_t r,
+                   uint32_t* B, int64_t ldb, int64_t ncols) {
+  const uint32_t* tinv = c->tri_inv.as<uint32_t>() + (o / kTB) * kTB * kTB;
+  if (r <= 4 * kTB) return launch_llu_strip<4>(c, L, ldl, r, tinv, B, ldb, ncols);
+  return launch_llu_strip<8>(c, L, ldl, r, tinv, B, ldb, ncols);
+}
+
+int trsm_ru_strip(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t o, int64_t r, uint32_t* B,
+                  int64_t ldb, int64_t nrows) {
+  const uint32_t* tinv = c->tri_inv.as<uint32_t>() + (o / kTB) * kTB * kTB;
+  if (r <= 4 * kTB) return launch_ru_strip<4>(c, U, ldu, r, tinv, B, ldb, nrows);
+  return launch_ru_strip<8>(c, U, ldu, r, tinv, B, ldb, nrows);
 }

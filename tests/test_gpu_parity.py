@@ -451,6 +451,25 @@ def test_pluq_tile_leaf(ctx, p, shape, frac):
         assert_parity(ctx, A, p, "limb")
 
 
+@pytest.mark.parametrize("strip", [0, 256, 512])
+@pytest.mark.parametrize("p,shape,frac", [(65521, (1500, 1400), 1.0), (131071, (900, 1300), 0.7),
+                                          (2147483647, (700, 650), 0.9), (3, (800, 800), 0.5)])
+def test_pluq_trsm_strips(ctx, strip, p, shape, frac):
+    """Triangular solves finished by strip launches (whole triangles of up to 256
+    or 512 rows per launch, ragged last blocks) equal the oracle, as the one-launch-
+    per-block path does."""
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(frac * min(m, n)), p, seed=15)
+    ctx.set_option("trsm_strip", strip)
+    try:
+        with leaf_mode(ctx, (96, 2)):
+            assert_parity(ctx, g.A, p, "limb")
+        with leaf_mode(ctx, (512, 2)):
+            assert_parity(ctx, g.A, p, "fp64")
+    finally:
+        ctx.set_option("trsm_strip", 512)
+
+
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
 def test_pluq_trsm_blocks(ctx, tb):
     p = 65521
