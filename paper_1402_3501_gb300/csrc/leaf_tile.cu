@@ -132,15 +132,17 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     const uint32_t piv = __shfl_sync(full, mine, src);
     const uint32_t inv =
         p == 2 ? 1u : (inv_table ? __ldg(inv_table + piv) : f_inv_euclid(piv, p));
+    // live chunks [lo, nchunk): before lo every column was a pivot column
+    // before this step (chunk src, whose last live column may be the new pivot,
+    // still receives the multipliers)
+    const unsigned live = __ballot_sync(full, pivmask != 0xFFu);
+    const int lo = live ? __ffs(live) - 1 : nchunk;
+    const int nlive = nchunk - lo;
     if (lane == src) pivmask |= 1u << jl;
     if (tid == 0) {
       prow[r] = istar;
       pcol[r] = j0;
     }
-    // live chunks [lo, nchunk): before lo every column is a pivot column
-    const unsigned live = __ballot_sync(full, pivmask != 0xFFu);
-    const int lo = live ? __ffs(live) - 1 : nchunk;
-    const int nlive = nchunk - lo;
     // this warp's rows below the pivot row: l_k = warp + 32 (kb + k), k < nr;
     // lane k computes row k's multiplier (its L entry)
     const int kb = istar < warp ? 0 : (istar - warp) / kTileWarps + 1;
