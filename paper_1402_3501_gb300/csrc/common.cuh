@@ -153,7 +153,7 @@ struct pluq_ctx {
   int form = PLUQ_FORM_FP64;
   int bm = 128, bn = 128;  // base-case tile
   int trsm_block = 64;     // diagonal block of the triangular solves
-  int strip_max = 512;     // largest triangle solved by one strip launch (0: none)
+  int strip_max = 0;       // largest triangle solved by one strip launch (0: none)
   int leaf_dim = 1024;     // cooperative leaves up to leaf_dim x leaf_dim (0: off)
   int leaf_kind = 2;       // 0: grid barrier per pivot, 1: wavefront, 2: chosen per leaf,
                            // 3: cluster barrier per pivot, 4: one-CTA 16-bit tile

@@ -467,7 +467,7 @@ def test_pluq_trsm_strips(ctx, strip, p, shape, frac):
         with leaf_mode(ctx, (512, 2)):
             assert_parity(ctx, g.A, p, "fp64")
     finally:
-        ctx.set_option("trsm_strip", 512)
+        ctx.set_option("trsm_strip", 0)
 
 
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
