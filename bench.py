@@ -387,6 +387,8 @@ def bench_ours(args, world, rank, local):
     if args.winograd_min:
         ctx.set_option("winograd_min", args.winograd_min)
     ctx.set_option("fgemm_tile", args.fgemm_tile)
+    ctx.set_option("fused_kmax", args.fused_kmax)
+    ctx.set_option("thin_gemm", 0 if args.no_thin else 1)
     if args.decomposition == "iterative":
         ctx.set_option("decomposition", 1)
         ctx.set_option("slab_rows", args.slab_rows)
@@ -588,6 +590,8 @@ def profile_fgemm(args):
     ctx = pq.Context(0)
     ctx.set_option("winograd_min", args.winograd_min)
     ctx.set_option("fgemm_tile", args.fgemm_tile)
+    ctx.set_option("fused_kmax", args.fused_kmax)
+    ctx.set_option("thin_gemm", 0 if args.no_thin else 1)
     form = "fp64" if args.form == "fp64" else "limb"
     ms = []
     for _ in range(max(1, args.repeat)):
@@ -598,7 +602,8 @@ def profile_fgemm(args):
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
-    print(f"fgemm {M}x{N}x{K} p={p} {form} tile={args.fgemm_tile} winograd_min={args.winograd_min}: "
+    print(f"fgemm {M}x{N}x{K} p={p} {form} tile={args.fgemm_tile} fused_kmax={args.fused_kmax} "
+          f"thin={0 if args.no_thin else 1} winograd_min={args.winograd_min}: "
           f"last {ms[-1]:.3f} ms "
           f"({2.0 * M * N * K / ms[-1] / 1e9:.1f} field Tops/s)", flush=True)
 
@@ -637,6 +642,10 @@ def main():
                     help="MxNxK: profiling case of one fgemm_modp call instead of the bench "
                          "(with --p, --form, --repeat)")
     ap.add_argument("--p", type=int, default=65521, help="prime of the --fgemm case")
+    ap.add_argument("--fused-kmax", type=int, default=0,
+                    help="limb products with K up to this split digits in the fgemm's producer")
+    ap.add_argument("--no-thin", action="store_true",
+                    help="no CUDA-core path for thin products (--fgemm case)")
     ap.add_argument("--fgemm-tile", type=int, default=0,
                     help="limb fgemm tile variant (0-2) of the --fgemm case, and of the bench "
                          "with --schedule (the autotuner picks it otherwise)")

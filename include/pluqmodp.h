@@ -318,6 +318,13 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        one launch per 64-block and per update between them,
  *                        which measured faster on the 32768^2 factorization.
  *                        Takes effect with PLUQ_OPT_TRSM_BLOCK 64.
+ *   PLUQ_OPT_FUSED_KMAX  [0, 2^31): limb-form products with an inner dimension
+ *                        K up to this value run the fused kernel, whose producer
+ *                        warps read the raw residues and split them into FP16
+ *                        digits in shared memory themselves (no separate
+ *                        packing launch; each element converted once per tile
+ *                        that reads it); longer products pack their digit
+ *                        planes once and stream them with TMA.  0: never.
  *   PLUQ_OPT_WORKSPACE_MB  cap on the device workspace the context (with its
  *                        child contexts) holds, in MiB [0, 2^31); 0 (default):
  *                        none.  A call whose workspace would exceed the cap
@@ -340,6 +347,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_WINOGRAD_MIN 14
 #define PLUQ_OPT_FGEMM_TILE 15
 #define PLUQ_OPT_TRSM_STRIP 16
+#define PLUQ_OPT_FUSED_KMAX 17
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

@@ -146,7 +146,8 @@ class Context:
     OPTIONS = {"leaf_dim": 1, "leaf_kind": 2, "tile_m": 3, "tile_n": 4, "trsm_block": 5,
                "chain_rows": 6, "fork_depth": 7, "use_tuned": 8, "thin_gemm": 9,
                "decomposition": 10, "slab_rows": 11, "wait_limit_us": 12, "workspace_mb": 13,
-               "winograd_min": 14, "fgemm_tile": 15, "trsm_strip": 16}
+               "winograd_min": 14, "fgemm_tile": 15, "trsm_strip": 16,
+               "fused_kmax": 17}
 
     def set_option(self, name: str, value: int):
         """Set a recursion option (see PLUQ_OPT_* in include/pluqmodp.h)."""

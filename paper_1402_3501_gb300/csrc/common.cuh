@@ -187,6 +187,7 @@ struct pluq_ctx {
   uint32_t limb_plan_p = 0;       // p of the cached limb fgemm plan
   uint64_t limb_plan[6] = {0, 0, 0, 0, 0, 0};
   int limb_variant = 0;           // tile variant of the limb fgemm (0, 1, 2)
+  int64_t fused_kmax = 0;         // limb fgemms with K up to this split digits in the producer
   // concurrent recursion (the independent calls on F and G): two child
   // contexts, each with its own stream, workspace and host thread; they share
   // the parent's index-vector slots and inverse table (disjoint ranges /

@@ -335,6 +335,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->limb_plan_p = c->limb_plan_p;
   for (int k = 0; k < 6; ++k) l->limb_plan[k] = c->limb_plan[k];
   l->limb_variant = c->limb_variant;
+  l->fused_kmax = c->fused_kmax;
   l->perm_r = c->perm_r;
   l->perm_c = c->perm_c;
   l->inv_table = c->inv_table;
@@ -1348,6 +1349,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_WAIT_LIMIT_US:
       if (value < 0 || value > 60000000) return PLUQ_ERR_INVALID_ARG;
       c->wait_cycles = (long long)value * 2000;
+      return PLUQ_OK;
+    case PLUQ_OPT_FUSED_KMAX:
+      if (value < 0) return PLUQ_ERR_INVALID_ARG;
+      c->fused_kmax = value;
       return PLUQ_OK;
     case PLUQ_OPT_TRSM_STRIP:
       if (value != 0 && value != 256 && value != 512) return PLUQ_ERR_INVALID_ARG;

@@ -615,6 +615,311 @@ int launch_pack(cudaStream_t s, const uint32_t* A, int64_t lda, int64_t M, int64
   return PLUQ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fused digit split: the same product with the digit split done by the
+// producer warps inside the fgemm instead of a separate packing pass.  Four
+// converter warps read raw uint32 tiles of A (128 x 64) and B (64 x TN) from
+// global memory, balance each residue, split it into its L signed base-2^8
+// digits and store the FP16 digit tiles straight into the shared-memory ring in
+// the layout the MMA descriptors expect (K-major rows of 128 bytes, 16-byte
+// chunks XOR-swizzled by the row index modulo 8, B transposed on the way), then
+// publish the stage through a proxy fence and an mbarrier arrival.  Every
+// element is converted once per tile that reads it (N/TN times for A, M/128
+// for B), against once per call for the packing pass, so this pays where K is
+// small and the packing launch and pipeline fill would dominate.
+constexpr int kFusedConv = 4;                                // converter warps
+constexpr int kFusedThreads = (kFusedConv + 1 + 8) * 32;     // + MMA warp + epilogue
+
+template <int L>
+struct FusedCfg {
+  static constexpr int TN = L <= 2 ? 128 : 64;
+  static constexpr int kAccs = 2 * L - 1;
+  static constexpr int kATile = kTileBytes;               // 128 x 64 FP16
+  static constexpr int kBTile = TN * kTK * 2;
+  static constexpr int kStageBytes = L * (kATile + kBTile);
+  static constexpr int kStages = (200 * 1024) / kStageBytes > 4 ? 4 : (200 * 1024) / kStageBytes;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr uint32_t kIdesc = idesc_f16(TN);
+  static constexpr int kEpiCols = TN / 2;
+  static constexpr int kChunk = L <= 2 ? 8 : 4;
+  static_assert(kAccs * TN <= 512, "accumulators exceed TMEM");
+  static_assert(kTM * (TN + 1) * 4 <= kStages * kStageBytes, "staging exceeds the ring");
+};
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int L>
+__device__ __forceinline__ uint4 digits_to_u4(const __half (&h)[8]) {
+  return *reinterpret_cast<const uint4*>(h);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_fgemm_limb_fused(const uint32_t* __restrict__ A, int64_t lda, const uint32_t* __restrict__ B,
+                       int64_t ldb, int64_t M, int64_t N, int64_t K, int num_kb, int group_kb,
+                       uint32_t* __restrict__ C, int64_t ldc, FieldP F, uint64_t bias,
+                       uint64_t bias_hi, int* __restrict__ err) {
+  using Cfg = FusedCfg<L>;
+  constexpr int TN = Cfg::TN;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + Cfg::kStages;
+  uint64_t* acc_full = bars + 2 * Cfg::kStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* mma_done = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = gridDim.x, tiles_m = gridDim.y;
+  const int lin = blockIdx.y * tiles_n + blockIdx.x;
+  const int band = lin / (kBandTiles * tiles_n);
+  const int first_m = band * kBandTiles;
+  const int band_h = min(tiles_m - first_m, kBandTiles);
+  const int in_band = lin - band * kBandTiles * tiles_n;
+  const int m0 = (first_m + in_band % band_h) * kTM, n0 = (in_band / band_h) * TN;
+  const int num_groups = (num_kb + group_kb - 1) / group_kb;
+  constexpr int kMmaWarp = kFusedConv;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], kFusedConv);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp < kFusedConv) {
+    // ------------------------------------------------- converter warps
+    const int ct = threadIdx.x;  // 0 .. 127
+    const uint32_t p = F.p;
+    const bool veca = ((reinterpret_cast<uintptr_t>(A) | (uintptr_t)(lda * 4)) & 15u) == 0;
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % Cfg::kStages;
+      const uint32_t ph = (kb / Cfg::kStages) & 1;
+      bool ok = true;
+      if (lane == 0) {
+        ok = mbar_wait(&empty[s], ph ^ 1, err);
+        if (!ok) *abort_flag = 1;
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || *(volatile int*)abort_flag) break;
+      uint8_t* st = smem + s * Cfg::kStageBytes;
+      const int64_t k0 = (int64_t)kb * kTK;
+      // A: 128 rows x 8 chunks of 8 k; 8 consecutive threads read one row
+#pragma unroll 2
+      for (int it = ct; it < kTM * 8; it += kFusedConv * 32) {
+        const int r = it >> 3, c = it & 7;
+        const int64_t gr = m0 + r, gk = k0 + 8 * c;
+        uint32_t a[8];
+        if (gr < M && veca && gk + 8 <= K) {
+          const uint4* src = reinterpret_cast<const uint4*>(A + gr * lda + gk);
+          const uint4 u0 = __ldg(src), u1 = __ldg(src + 1);
+          a[0] = u0.x; a[1] = u0.y; a[2] = u0.z; a[3] = u0.w;
+          a[4] = u1.x; a[5] = u1.y; a[6] = u1.z; a[7] = u1.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a[q] = (gr < M && gk + q < K) ? __ldg(A + gr * lda + gk + q) : 0u;
+        }
+        __align__(16) __half h[L][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          __half d[L];
+          split_digits<L>(balance(a[q], p), d);
+#pragma unroll
+          for (int l = 0; l < L; ++l) h[l][q] = d[l];
+        }
+        const int off = r * 128 + ((c ^ (r & 7)) << 4);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+          *reinterpret_cast<uint4*>(st + l * Cfg::kATile + off) =
+              *reinterpret_cast<const uint4*>(h[l]);
+      }
+      // B^T: TN rows (columns of B) x 8 chunks; 32 consecutive threads read 32
+      // consecutive columns of one row of B at a time
+#pragma unroll 2
+      for (int it = ct; it < TN * 8; it += kFusedConv * 32) {
+        const int n = it % TN, c = it / TN;
+        const int64_t gn = n0 + n, gk = k0 + 8 * c;
+        uint32_t b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = (gn < N && gk + q < K) ? __ldg(B + (gk + q) * ldb + gn) : 0u;
+        __align__(16) __half h[L][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          __half d[L];
+          split_digits<L>(balance(b[q], p), d);
+#pragma unroll
+          for (int l = 0; l < L; ++l) h[l][q] = d[l];
+        }
+        const int off = n * 128 + ((c ^ (n & 7)) << 4);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+          *reinterpret_cast<uint4*>(st + L * Cfg::kATile + l * Cfg::kBTile + off) =
+              *reinterpret_cast<const uint4*>(h[l]);
+      }
+      // the generic-proxy stores become visible to the tensor core's reads
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ---------------------------------------------------- MMA issuer
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % Cfg::kStages;
+        const int g = kb / group_kb;
+        const bool first = (kb % group_kb) == 0;
+        const bool last = (kb % group_kb) == group_kb - 1 || kb == num_kb - 1;
+        if (first && g > 0) {
+          if (!mbar_wait(acc_empty, (g - 1) & 1, err)) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+        if (!mbar_wait(&full[s], (kb / Cfg::kStages) & 1, err)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
+#pragma unroll
+        for (int kk = 0; kk < kTK / 16; ++kk) {
+          uint32_t seen = 0;
+#pragma unroll
+          for (int i = 0; i < L; ++i) {
+            const uint64_t da = smem_desc_sw128(st + i * Cfg::kATile + kk * 32);
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+              const uint64_t db = smem_desc_sw128(st + L * Cfg::kATile + j * Cfg::kBTile + kk * 32);
+              const int w = i + j;
+              const uint32_t acc = (first && kk == 0 && !((seen >> w) & 1u)) ? 0u : 1u;
+              seen |= 1u << w;
+              umma_f16(tmem + (uint32_t)(w * TN), da, db, Cfg::kIdesc, acc);
+            }
+          }
+        }
+        umma_commit(&empty[s]);
+        if (last) umma_commit(acc_full);
+      }
+      umma_commit(mma_done);
+      mbar_wait(mma_done, 0, err);
+    }
+  } else {
+    // -------------------------------------------------------- epilogue
+    const int e = warp - kMmaWarp - 1;  // 0 .. 7
+    const int q = warp & 3;             // the TMEM lane quadrant this warp may access
+    const int h = e >> 2;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    constexpr int EC = Cfg::kEpiCols;
+    constexpr int CW = Cfg::kChunk;
+    uint32_t res[EC];
+#pragma unroll
+    for (int i = 0; i < EC; ++i) res[i] = 0u;
+    bool ok = true;
+    for (int g = 0; g < num_groups; ++g) {
+      if (!mbar_wait(acc_full, g & 1, err)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t set = lane_base + (uint32_t)(h * EC);
+#pragma unroll
+      for (int ch = 0; ch < EC / CW; ++ch) {
+        uint32_t c[Cfg::kAccs][CW];
+#pragma unroll
+        for (int w = 0; w < Cfg::kAccs; ++w) tmem_ldw<CW>(set + w * TN + ch * CW, c[w]);
+        tmem_wait_ld();
+        if (ch == EC / CW - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
+        }
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+          uint32_t v;
+          if (L <= 2) {
+            int64_t t = 0;
+#pragma unroll
+            for (int w = 0; w < Cfg::kAccs; ++w)
+              t += (int64_t)__float2int_rn(__uint_as_float(c[w][i])) * (1 << (kLimbBits * w));
+            v = F.is2 ? (uint32_t)((uint64_t)(t + (int64_t)bias) & 1u)
+                      : f_redc((uint64_t)(t + (int64_t)bias), F);
+          } else {
+            int64_t tlo = 0, thi = 0;
+#pragma unroll
+            for (int w = 0; w < Cfg::kAccs; ++w) {
+              const int64_t cw = (int64_t)__float2int_rn(__uint_as_float(c[w][i]));
+              if (w < 4)
+                tlo += cw * ((int64_t)1 << (kLimbBits * w));
+              else
+                thi += cw * ((int64_t)1 << (kLimbBits * (w - 4)));
+            }
+            const uint32_t vlo = f_redc((uint64_t)(tlo + (int64_t)bias), F);
+            const uint32_t vhi = f_redc((uint64_t)(thi + (int64_t)bias_hi), F);
+            v = f_add(vlo, f_redc((uint64_t)vhi * F.r2, F), F);
+          }
+          res[ch * CW + i] = f_add(res[ch * CW + i], v, F);
+        }
+      }
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (ok) {
+      uint32_t* stage = reinterpret_cast<uint32_t*>(smem) + row * (TN + 1) + h * EC;
+#pragma unroll
+      for (int i = 0; i < EC; ++i) stage[i] = F.is2 ? res[i] : f_redc((uint64_t)res[i] * F.r2, F);
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    if (*(volatile int*)abort_flag == 0) {
+      const uint32_t* stage = reinterpret_cast<const uint32_t*>(smem);
+      for (int rr = e; rr < kTM; rr += 8) {
+        const int64_t gr = (int64_t)m0 + rr;
+        if (gr >= M) break;
+        uint32_t* crow = C + gr * ldc + n0;
+        constexpr int NQ = (TN + 31) / 32;
+        uint32_t cv[NQ];
+#pragma unroll
+        for (int q2 = 0; q2 < NQ; ++q2) {
+          const int j = lane + 32 * q2;
+          cv[q2] = (j < TN && n0 + j < N) ? crow[j] : 0u;
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < NQ; ++q2) {
+          const int j = lane + 32 * q2;
+          if (j < TN && n0 + j < N) crow[j] = f_sub(cv[q2], stage[rr * (TN + 1) + j], F);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 // ------------------------------------------------------------ host side --
 
 struct LimbPlan {
@@ -784,6 +1089,28 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   return PLUQ_OK;
 }
 
+template <int L>
+int run_limb_fused(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K,
+                   const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb, uint32_t* C,
+                   int64_t ldc) {
+  using Cfg = FusedCfg<L>;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_fgemm_limb_fused<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+  PLUQ_CUDA(attr);
+  constexpr int TN = Cfg::TN;
+  const int64_t Mt = cdiv(M, kTM), Nt = cdiv(N, TN), Kp = cdiv(K, kTK) * kTK;
+  if (Mt > 65535 || Nt > INT32_MAX || Kp > INT32_MAX) return PLUQ_ERR_INVALID_ARG;
+  const dim3 grid((unsigned)Nt, (unsigned)Mt);
+  int* err = c->small.as<int>() + 16;
+  ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K, 4.0 * (M * K + K * N) + 8.0 * M * N, 1,
+               2.0 * Mt * kTM * Nt * TN * Kp * L * L);
+  k_fgemm_limb_fused<L><<<grid, kFusedThreads, Cfg::kSmem, c->stream>>>(
+      A, lda, B, ldb, M, N, K, (int)(Kp / kTK), pl.group_kb, C, ldc, c->F, pl.bias, pl.bias_hi,
+      err);
+  PLUQ_CUDA(cudaGetLastError());
+  return PLUQ_OK;
+}
+
 }  // namespace
 
 int limb_form_supported(uint32_t p) { return plan_for(p).L > 0; }
@@ -809,6 +1136,14 @@ int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
   cached.bias_hi = c->limb_plan[3];
   cached.group_kb_split = (int)c->limb_plan[4];
   cached.bias_split = c->limb_plan[5];
+  // a short inner dimension: the producer warps split the digits themselves
+  // (no packing launch, one pass over the operands per tile)
+  if (K <= c->fused_kmax) {
+    if (cached.L == 1) return run_limb_fused<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+    if (cached.L == 2) return run_limb_fused<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+    if (cached.L == 3) return run_limb_fused<3>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+    if (cached.L == 4) return run_limb_fused<4>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
+  }
   const int v = c->limb_variant;
   if (cached.L == 1)
     return v == 2 ? run_limb<1, 2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc)

@@ -143,6 +143,57 @@ def test_fgemm_tile_variants(ctx, tile, p, mnk):
     assert np.array_equal(Cd.cpu().numpy().astype(np.int64), expect)
 
 
+@pytest.mark.parametrize("p", [2, 251, 65521, 131071, 1048573, 2147483647])
+@pytest.mark.parametrize("mnk", [(1, 1, 1), (70, 33, 17), (129, 257, 64), (300, 200, 130),
+                                 (200, 300, 2100)])
+def test_fgemm_fused_split(ctx, p, mnk):
+    """The fgemm whose producer warps split the digits (no packing pass) gives
+    exactly C - A B mod p: every digit count, ragged tiles, K spanning several
+    exact groups, operands at p - 1, and strided (unaligned) views."""
+    M, N, K = mnk
+    rng = np.random.default_rng(M + 5 * N + K + p % 83)
+    A = rng.integers(0, p, (M, K), dtype=np.int64)
+    B = rng.integers(0, p, (K, N), dtype=np.int64)
+    C = rng.integers(0, p, (M, N), dtype=np.int64)
+    A[: (M + 1) // 2, :] = p - 1
+    B[:, : (N + 2) // 3] = p - 1
+    expect = (C - matmul_mod(A, B, p)) % p
+    ctx.set_option("fused_kmax", 1 << 30)
+    ctx.set_option("thin_gemm", 0)
+    try:
+        Cd = to_dev(C)
+        pq.fgemm_modp(Cd, to_dev(A), to_dev(B), p, form="limb", ctx=ctx)
+        # the same product on views with odd leading dimensions
+        big = torch.zeros((M + 3, K + N + 7), dtype=torch.int32, device="cuda")
+        Av = big[1:M + 1, 3:K + 3]
+        Av.copy_(to_dev(A))
+        bigb = torch.zeros((K + 2, N + 5), dtype=torch.int32, device="cuda")
+        Bv = bigb[1:K + 1, 1:N + 1]
+        Bv.copy_(to_dev(B))
+        Cv = to_dev(C)
+        pq.fgemm_modp(Cv, Av, Bv, p, form="limb", ctx=ctx)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option("fused_kmax", 0)
+        ctx.set_option("thin_gemm", 1)
+    assert np.array_equal(Cd.cpu().numpy().astype(np.int64) % (1 << 32), expect)
+    assert np.array_equal(Cv.cpu().numpy().astype(np.int64) % (1 << 32), expect)
+
+
+@pytest.mark.parametrize("kmax", [128, 512])
+@pytest.mark.parametrize("p,shape,frac", [(65521, (1100, 900), 1.0), (131071, (777, 700), 0.6),
+                                          (2147483647, (600, 650), 0.8)])
+def test_pluq_fused_split(ctx, kmax, p, shape, frac):
+    m, n = shape
+    g = workloads.prescribed_rank_matrix(m, n, int(frac * min(m, n)), p, seed=16)
+    ctx.set_option("fused_kmax", kmax)
+    try:
+        with leaf_mode(ctx, (128, 2)):
+            assert_parity(ctx, g.A, p, "limb")
+    finally:
+        ctx.set_option("fused_kmax", 0)
+
+
 @pytest.mark.parametrize("tile", [1, 2])
 @pytest.mark.parametrize("p,shape,frac", [(65521, (1100, 900), 1.0), (131071, (777, 700), 0.6)])
 def test_pluq_tile_variants(ctx, tile, p, shape, frac):
