@@ -325,6 +325,13 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        packing launch; each element converted once per tile
  *                        that reads it); longer products pack their digit
  *                        planes once and stream them with TMA.  0: never.
+ *   PLUQ_OPT_DIAG_INVERSES  1 (default): the inverses of the triangles of
+ *                        every full-rank square leaf on the matrix's diagonal are
+ *                        computed once (leaf cut-off squared each, kept in the
+ *                        workspace), and the triangular solves of its ancestors
+ *                        stop at that size and apply them as single tensor-core
+ *                        products; used while no recursion node so far met a
+ *                        rank-deficient leading block.  0: off.
  *   PLUQ_OPT_WORKSPACE_MB  cap on the device workspace the context (with its
  *                        child contexts) holds, in MiB [0, 2^31); 0 (default):
  *                        none.  A call whose workspace would exceed the cap
@@ -348,6 +355,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_FGEMM_TILE 15
 #define PLUQ_OPT_TRSM_STRIP 16
 #define PLUQ_OPT_FUSED_KMAX 17
+#define PLUQ_OPT_DIAG_INVERSES 18
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

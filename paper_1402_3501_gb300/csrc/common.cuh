@@ -188,6 +188,15 @@ struct pluq_ctx {
   uint64_t limb_plan[6] = {0, 0, 0, 0, 0, 0};
   int limb_variant = 0;           // tile variant of the limb fgemm (0, 1, 2)
   int64_t fused_kmax = 0;         // limb fgemms with K up to this split digits in the producer
+  bool fgemm_beta0 = false;       // limb fgemm writes C = -A B (C's old values unread)
+  // inverses of full-rank square diagonal leaves (negated, b x b each, slot
+  // k for the leaf at rows and columns [k b, (k + 1) b) of the whole matrix):
+  // the triangular solves of every ancestor apply them as one product each
+  DevBuf dinv;                    // [slots][2][b][b]: -L^-1, -U^-1
+  std::vector<char> dinv_valid;   // per slot
+  int64_t dinv_b = 0;             // block size (the leaf cut-off), 0: cache off
+  std::atomic<bool> dinv_ok{false};  // no node so far had a rank-deficient A1 (no shifts)
+  int dinv_enable = 1;            // option
   // concurrent recursion (the independent calls on F and G): two child
   // contexts, each with its own stream, workspace and host thread; they share
   // the parent's index-vector slots and inverse table (disjoint ranges /
@@ -229,7 +238,8 @@ struct pluq_ctx {
 inline void bind_workspace(pluq_ctx* c) {
   for (DevBuf* b : {&c->scratch, &c->pack, &c->perm_r, &c->perm_c, &c->tmp_i, &c->tri_inv,
                     &c->small, &c->inv_table, &c->work, &c->leaf, &c->batch_dev,
-                    &c->batch_scratch, &c->batch_pq, &c->tune_src, &c->tune_dst, &c->wino})
+                    &c->batch_scratch, &c->batch_pq, &c->tune_src, &c->tune_dst, &c->wino,
+                    &c->dinv})
     b->acct = c->ws;
 }
 
@@ -285,10 +295,14 @@ int permute_rows2(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t rows, int64_t c
 // columns of A permuted over rows [r0, r0 + m0) and [r1, r1 + m1) at once
 int permute_cols2(pluq_ctx* c, uint32_t* A, int64_t lda, int64_t r0, int64_t m0, int64_t r1,
                   int64_t m1, int64_t cols, const int32_t* perm);
+// diag0: the triangle's offset on the whole matrix's diagonal (-1: not on it),
+// for the cached inverses of full-rank diagonal leaves
 int trsm_left_lower_unit(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r, uint32_t* B,
-                         int64_t ldb, int64_t ncols);
+                         int64_t ldb, int64_t ncols, int64_t diag0 = -1);
 int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
-                     int64_t ldb, int64_t nrows);
+                     int64_t ldb, int64_t nrows, int64_t diag0 = -1);
+// -L^{-1}, -U^{-1} of the full-rank dinv_b x dinv_b block T into cache slot `slot`
+int cache_leaf_inverses(pluq_ctx* c, const uint32_t* T, int64_t ldt, int64_t slot);
 int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
                     int64_t ldb, int64_t ncols);
 // one-launch solves of a triangle of at most strip_rows(c, count) rows (its

@@ -482,13 +482,14 @@ struct Recursion {
     PLUQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
     PLUQ_CUDA(cudaStreamWaitEvent(lg->stream, c->fork_ev, 0));
     // G's stream: E, then G -= E V1
-    PLUQ_TRY(trsm_right_upper(lg, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2));
+    const int64_t diag0 = R0 == C0 ? R0 : -1;
+    PLUQ_TRY(trsm_right_upper(lg, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2, diag0));
     PLUQ_CUDA(cudaEventRecord(c->side_ev[0], lg->stream));
     PLUQ_TRY(fgemm_sub(lg, m2, n1 - r1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, r1), lda,
                        X(R0, C0, m1, r1), lda));
     PLUQ_CUDA(cudaEventRecord(c->side_ev[1], lg->stream));
     // this stream: D, then [F; H] -= [M1; E] D once E is ready
-    PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2));
+    PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2, diag0));
     PLUQ_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[0], 0));
     PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
                        X(R0, C0, r1, n1), lda));
@@ -566,6 +567,12 @@ struct Recursion {
       id->c = c->host_small[13] != 0;
       if (tile || chain || cluster || leaf)
         c->leaf_density = (double)*r_out / (double)std::min(m, n);
+      const int64_t b = c->dinv_b;
+      if (b > 0 && c->dinv_ok && m == b && n == b && *r_out == b && R0 == C0 && R0 % b == 0 &&
+          R0 / b < (int64_t)c->dinv_valid.size()) {
+        PLUQ_TRY(cache_leaf_inverses(c, X(R0, C0, 0, 0), lda, R0 / b));
+        c->dinv_valid[R0 / b] = 1;
+      }
       return PLUQ_OK;
     }
     if (d + 2 >= c->depth_slots) return PLUQ_ERR_INVALID_ARG;  // the last slot is scratch
@@ -606,6 +613,11 @@ struct Recursion {
     int64_t r1 = 0;
     Ident id1, id2, id3, id4;
     PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1, &id1, KEEP_LU));
+    if (r1 < m1 || r1 < n1) {
+      // F or G is non-empty: blocks move by shifts, the diagonal blocks of later
+      // triangles are no longer the cached leaves
+      for (pluq_ctx* o = c; o; o = o->parent) o->dinv_ok = false;
+    }
     PLUQ_TRY(compose_pair(pr, cr + R0, m1, pc, cc + C0, n1, id1));
     if (!id1.r) PLUQ_TRY(permute_rows(c, X(R0, C0, 0, n1), lda, m1, n2, cr + R0));
     if (!id1.c) PLUQ_TRY(permute_cols(c, X(R0, C0, m1, 0), lda, m2, n1, cc + C0));
@@ -618,8 +630,10 @@ struct Recursion {
       if (side) {
         PLUQ_TRY(side_stream_update(R0, C0, m1, n1, m2, n2, r1));
       } else {
-        PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2));
-        PLUQ_TRY(trsm_right_upper(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2));
+        const int64_t diag0 = R0 == C0 ? R0 : -1;
+        PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2,
+                                      diag0));
+        PLUQ_TRY(trsm_right_upper(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, m1, 0), lda, m2, diag0));
         PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
                            X(R0, C0, r1, n1), lda));
         PLUQ_TRY(fgemm_sub(c, m2, n1 - r1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, r1), lda,
@@ -795,6 +809,19 @@ int factor(pluq_ctx* c, int64_t m, int64_t n, uint32_t* A, int64_t lda, int64_t*
     PLUQ_CUDA(cudaStreamSynchronize(c->stream));
     if (c->host_small[0] != 0) return PLUQ_ERR_ENTRY_OUT_OF_RANGE;
   }
+  // inverses of the full-rank diagonal leaves, for the solves of every ancestor
+  c->dinv_b = 0;
+  c->dinv_ok = false;
+  c->dinv_valid.clear();
+  if (c->dinv_enable && c->decomposition == 0 && c->leaf_dim > 0 && c->lane_depth == 0 &&
+      std::min(m, n) >= 2 * (int64_t)c->leaf_dim) {
+    const int64_t b = c->leaf_dim, slots = std::min(m, n) / b;
+    if (c->dinv.ensure(sizeof(uint32_t) * slots * 2 * b * b) == PLUQ_OK) {
+      c->dinv_b = b;
+      c->dinv_ok = true;
+      c->dinv_valid.assign(slots, 0);
+    }
+  }
   Recursion rec{c, A, lda, c->small.as<int32_t>() + 8};
   Ident id;
   PLUQ_TRY(rec.node(0, 0, m, n, 0, r_out, &id, keep));
@@ -942,6 +969,7 @@ int pluq_destroy(pluq_ctx* c) {
   if (c->batch_host) cudaFreeHost(c->batch_host);
   c->work.release();
   c->wino.release();
+  c->dinv.release();
   if (c->host_small) cudaFreeHost(c->host_small);
   delete c;
   return PLUQ_OK;
@@ -1349,6 +1377,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_WAIT_LIMIT_US:
       if (value < 0 || value > 60000000) return PLUQ_ERR_INVALID_ARG;
       c->wait_cycles = (long long)value * 2000;
+      return PLUQ_OK;
+    case PLUQ_OPT_DIAG_INVERSES:
+      if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;
+      c->dinv_enable = value;
       return PLUQ_OK;
     case PLUQ_OPT_FUSED_KMAX:
       if (value < 0) return PLUQ_ERR_INVALID_ARG;

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     k_fgemm_limb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int64_t M, int64_t N, int Mp, int Np, int num_kb, int group_kb,
                  uint32_t* __restrict__ C, int64_t ldc, FieldP F, uint64_t bias,
-                 uint64_t bias_hi, int* __restrict__ err) {
+                 uint64_t bias_hi, int* __restrict__ err, int beta0) {
   using Cfg = LimbCfg<L, V>;
   constexpr int TN = Cfg::TN;
   extern __shared__ uint8_t smem_raw[];
@@ -438,7 +438,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
       for (int e = 0; e < EC; ++e) stage[e] = F.is2 ? res[e] : f_redc((uint64_t)res[e] * F.r2, F);
     }
-    // C <- C - residue, one warp per row, 32 consecutive columns per access
+    // C <- C - residue (C <- -residue when beta0: the product overwrites C,
+    // whose old values are never read), one warp per row, 32 consecutive
+    // columns per access
     asm volatile("bar.sync 1, 256;" ::: "memory");
     if (*(volatile int*)abort_flag == 0) {
       const int ew = warp - 2;
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
         for (int q2 = 0; q2 < NQ; ++q2) {
           const int j = lane + 32 * q2;
-          cv[q2] = (j < TN && n0 + j < N) ? crow[j] : 0u;
+          cv[q2] = (!beta0 && j < TN && n0 + j < N) ? crow[j] : 0u;
         }
 #pragma unroll
         for (int q2 = 0; q2 < NQ; ++q2) {
@@ -1084,7 +1086,7 @@ int run_limb(pluq_ctx* c, const LimbPlan& pl, int64_t M, int64_t N, int64_t K, c
   k_fgemm_limb<L, V><<<grid, kGemmThreads, Cfg::kSmem, c->stream>>>(
       ma, mb, M, N, (int)Mp, (int)Np, (int)(Kp / kTK),
       Cfg::kSplit ? pl.group_kb_split : pl.group_kb, C, ldc, c->F,
-      Cfg::kSplit ? pl.bias_split : pl.bias, pl.bias_hi, err);
+      Cfg::kSplit ? pl.bias_split : pl.bias, pl.bias_hi, err, c->fgemm_beta0 ? 1 : 0);
   PLUQ_CUDA(cudaGetLastError());
   return PLUQ_OK;
 }
@@ -1138,7 +1140,7 @@ int fgemm_sub_limb(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
   cached.bias_split = c->limb_plan[5];
   // a short inner dimension: the producer warps split the digits themselves
   // (no packing launch, one pass over the operands per tile)
-  if (K <= c->fused_kmax) {
+  if (K <= c->fused_kmax && !c->fgemm_beta0) {
     if (cached.L == 1) return run_limb_fused<1>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
     if (cached.L == 2) return run_limb_fused<2>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
     if (cached.L == 3) return run_limb_fused<3>(c, cached, M, N, K, A, lda, B, ldb, C, ldc);
@@ -1252,7 +1254,7 @@ int noalloc_run(const NoAllocDevice& d, const LimbPlan& pl, const FieldP& F, int
   const dim3 grid((unsigned)(Np / TN), (unsigned)(Mp / kTM));
   k_fgemm_limb<L, 0><<<grid, kGemmThreads, Cfg::kSmem, s>>>(ma, mb, M, N, (int)Mp, (int)Np,
                                                          (int)(Kp / kTK), pl.group_kb, C, ldc, F,
-                                                         pl.bias, pl.bias_hi, d.err);
+                                                         pl.bias, pl.bias_hi, d.err, 0);
   PLUQ_CUDA(cudaGetLastError());
   // the kernel's error word (a bounded wait that ran out leaves C as it was)
   // comes back to the host: the call returns once the product is done

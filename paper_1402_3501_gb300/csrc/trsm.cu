@@ -300,20 +300,147 @@ int lu_rec(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t o, int64_t r, ui
   return lu_rec(c, U, ldu, o, r1, B, ldb, ncols);
 }
 
+// ---------------------------------------------- cached diagonal inverses --
+//
+// When the diagonal b x b blocks of a triangle are full-rank square leaves of
+// the recursion, their inverses were computed once when the leaf was factored
+// (negated: -L^{-1}, -U^{-1}); every ancestor's solve then recurses only down
+// to b and applies each diagonal block as one product X = Inv B with the
+// product overwriting B (the limb fgemm's operands are packed before it writes,
+// so the update is in place; the other forms go through scratch).
+
+__global__ void k_copy_block(uint32_t* __restrict__ dst, int64_t ldd, const uint32_t* __restrict__ src,
+                             int64_t lds, int64_t rows, int64_t cols) {
+  for (int64_t t = blockIdx.y; t < rows; t += gridDim.y)
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < cols;
+         u += (int64_t)gridDim.x * blockDim.x)
+      dst[t * ldd + u] = src ? src[t * lds + u] : 0u;
+}
+
+dim3 block_grid(int64_t rows, int64_t cols) {
+  int64_t gx = cdiv(cols, 256);
+  if (gx > 32) gx = 32;
+  const int64_t gy = rows < 65535 ? rows : 65535;
+  return dim3((unsigned)(gx < 1 ? 1 : gx), (unsigned)(gy < 1 ? 1 : gy), 1);
+}
+
+// C (rows x cols) <- -(X Y) mod p, X rows x k, Y k x cols; C may be X or Y.
+int product_overwrite(pluq_ctx* c, int64_t rows, int64_t cols, int64_t k, const uint32_t* X,
+                      int64_t ldx, const uint32_t* Y, int64_t ldy, uint32_t* C, int64_t ldc) {
+  if (c->form == PLUQ_FORM_LIMB_F16) {
+    c->fgemm_beta0 = true;
+    const int st = fgemm_sub_limb(c, rows, cols, k, X, ldx, Y, ldy, C, ldc);
+    c->fgemm_beta0 = false;
+    return st;
+  }
+  // the other forms read C: copy the operand C aliases to scratch, zero C
+  PLUQ_TRY(c->scratch.ensure(sizeof(uint32_t) * rows * cols));
+  uint32_t* S = c->scratch.as<uint32_t>();
+  const bool left = (const uint32_t*)C == Y;  // C is Y (rows = k) or X (cols = k)
+  {
+    ProfScope ps(c, PC_TRSM, 0, 12.0 * rows * cols, 2);
+    k_copy_block<<<block_grid(rows, cols), 256, 0, c->stream>>>(S, cols, C, ldc, rows, cols);
+    k_copy_block<<<block_grid(rows, cols), 256, 0, c->stream>>>(C, ldc, nullptr, 0, rows, cols);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  if (left) return fgemm_sub_classical(c, rows, cols, k, X, ldx, S, cols, C, ldc);
+  return fgemm_sub_classical(c, rows, cols, k, S, cols, Y, ldy, C, ldc);
+}
+
+const uint32_t* cached_inv(const pluq_ctx* owner, int64_t slot, int which) {
+  const int64_t b = owner->dinv_b;
+  return owner->dinv.as<uint32_t>() + (slot * 2 + which) * b * b;
+}
+
+int llu_cached(pluq_ctx* c, const pluq_ctx* owner, const uint32_t* L, int64_t ldl, int64_t slot,
+               int64_t r, uint32_t* B, int64_t ldb, int64_t ncols) {
+  const int64_t b = owner->dinv_b;
+  if (r == b) return product_overwrite(c, b, ncols, b, cached_inv(owner, slot, 0), b, B, ldb, B, ldb);
+  const int64_t r1 = (r / 2 + b - 1) / b * b;
+  PLUQ_TRY(llu_cached(c, owner, L, ldl, slot, r1, B, ldb, ncols));
+  PLUQ_TRY(fgemm_sub(c, r - r1, ncols, r1, L + r1 * ldl, ldl, B, ldb, B + r1 * ldb, ldb));
+  return llu_cached(c, owner, L + r1 * ldl + r1, ldl, slot + r1 / b, r - r1, B + r1 * ldb, ldb,
+                    ncols);
+}
+
+int ru_cached(pluq_ctx* c, const pluq_ctx* owner, const uint32_t* U, int64_t ldu, int64_t slot,
+              int64_t r, uint32_t* B, int64_t ldb, int64_t nrows) {
+  const int64_t b = owner->dinv_b;
+  if (r == b) return product_overwrite(c, nrows, b, b, B, ldb, cached_inv(owner, slot, 1), b, B, ldb);
+  const int64_t r1 = (r / 2 + b - 1) / b * b;
+  PLUQ_TRY(ru_cached(c, owner, U, ldu, slot, r1, B, ldb, nrows));
+  PLUQ_TRY(fgemm_sub(c, nrows, r - r1, r1, B, ldb, U + r1, ldu, B + r1, ldb));
+  return ru_cached(c, owner, U + r1 * ldu + r1, ldu, slot + r1 / b, r - r1, B + r1, ldb, nrows);
+}
+
+// The context holding cached inverses for the r x r triangle at diagonal
+// offset diag0 (c or its ancestors), or null when a block is missing.
+const pluq_ctx* cache_owner(const pluq_ctx* c, int64_t diag0, int64_t r) {
+  for (const pluq_ctx* o = c; o; o = o->parent) {
+    const int64_t b = o->dinv_b;
+    if (b <= 0 || !o->dinv_ok || diag0 < 0 || r <= 0 || diag0 % b || r % b) continue;
+    const int64_t s0 = diag0 / b, s1 = s0 + r / b;
+    if (s1 > (int64_t)o->dinv_valid.size()) continue;
+    bool all = true;
+    for (int64_t s = s0; s < s1 && all; ++s) all = o->dinv_valid[s] != 0;
+    if (all) return o;
+  }
+  return nullptr;
+}
+
 }  // namespace
 
 int trsm_left_lower_unit(pluq_ctx* c, const uint32_t* L, int64_t ldl, int64_t r, uint32_t* B,
-                         int64_t ldb, int64_t ncols) {
+                         int64_t ldb, int64_t ncols, int64_t diag0) {
   if (r <= 1 || ncols <= 0) return PLUQ_OK;  // a unit 1x1 triangle is the identity
+  if (const pluq_ctx* o = cache_owner(c, diag0, r))
+    return llu_cached(c, o, L, ldl, diag0 / o->dinv_b, r, B, ldb, ncols);
   PLUQ_TRY(invert_diag_blocks(c, kLowerUnitLeft, L, ldl, r));
   return llu_rec(c, L, ldl, 0, r, B, ldb, ncols);
 }
 
 int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
-                     int64_t ldb, int64_t nrows) {
+                     int64_t ldb, int64_t nrows, int64_t diag0) {
   if (r <= 0 || nrows <= 0) return PLUQ_OK;
+  if (const pluq_ctx* o = cache_owner(c, diag0, r))
+    return ru_cached(c, o, U, ldu, diag0 / o->dinv_b, r, B, ldb, nrows);
   PLUQ_TRY(invert_diag_blocks(c, kUpperRight, U, ldu, r));
   return ru_rec(c, U, ldu, 0, r, B, ldb, nrows);
+}
+
+// -(L^{-1}) and -(U^{-1}) of the b x b full-rank block T (compressed L\U) into
+// cache slot `slot` of c: the identity solved against each triangle, negated.
+__global__ void k_identity(uint32_t* __restrict__ X, int64_t b) {
+  for (int64_t i = blockIdx.y; i < b; i += gridDim.y)
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < b;
+         j += (int64_t)gridDim.x * blockDim.x)
+      X[i * b + j] = i == j ? 1u : 0u;
+}
+
+__global__ void k_negate(uint32_t* __restrict__ X, int64_t count, uint32_t p) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x)
+    X[t] = X[t] == 0u ? 0u : p - X[t];
+}
+
+int cache_leaf_inverses(pluq_ctx* c, const uint32_t* T, int64_t ldt, int64_t slot) {
+  const int64_t b = c->dinv_b;
+  uint32_t* Li = c->dinv.as<uint32_t>() + (slot * 2) * b * b;
+  uint32_t* Ui = Li + b * b;
+  {
+    ProfScope ps(c, PC_TRSM, 0, 8.0 * b * b, 2);
+    k_identity<<<block_grid(b, b), 256, 0, c->stream>>>(Li, b);
+    k_identity<<<block_grid(b, b), 256, 0, c->stream>>>(Ui, b);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  PLUQ_TRY(trsm_left_lower_unit(c, T, ldt, b, Li, b, b, -1));
+  PLUQ_TRY(trsm_right_upper(c, T, ldt, b, Ui, b, b, -1));
+  {
+    ProfScope ps(c, PC_TRSM, 0, 16.0 * b * b);
+    k_negate<<<(unsigned)cdiv(2 * b * b, 256 * 8), 256, 0, c->stream>>>(Li, 2 * b * b, c->F.p);
+    PLUQ_CUDA(cudaGetLastError());
+  }
+  return PLUQ_OK;
 }
 
 int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,

@@ -521,6 +521,32 @@ def test_pluq_trsm_strips(ctx, strip, p, shape, frac):
         ctx.set_option("trsm_strip", 0)
 
 
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("fork_depth", [0, 2])
+@pytest.mark.parametrize("leaf", [(128, 1), (96, 3), (256, 2)])
+@pytest.mark.parametrize("p,shape,kind", [(65521, (1024, 1024), "uniform"),
+                                          (131071, (1000, 1100), "uniform"),
+                                          (3, (900, 900), "uniform"),
+                                          (65521, (1024, 1024), "lru")])
+def test_pluq_cached_diagonal_inverses(ctx, form, fork_depth, leaf, p, shape, kind):
+    """Triangular solves that apply the cached inverses of full-rank diagonal
+    leaves (one product per leaf-sized block, in place) equal the oracle; ragged
+    edges, rank-deficient blocks (p = 3, prescribed rank) and concurrent branches
+    fall back where a block is missing."""
+    m, n = shape
+    A = (workloads.uniform_matrix(m, n, p, 17) if kind == "uniform"
+         else workloads.prescribed_rank_matrix(m, n, m // 2, p, 17).A)
+    ctx.set_option("fork_depth", fork_depth)
+    try:
+        for on in (1, 0):
+            ctx.set_option("diag_inverses", on)
+            with leaf_mode(ctx, leaf):
+                assert_parity(ctx, A, p, form)
+    finally:
+        ctx.set_option("diag_inverses", 1)
+        ctx.set_option("fork_depth", 2)
+
+
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
 def test_pluq_trsm_blocks(ctx, tb):
     p = 65521
