@@ -40,7 +40,11 @@ METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-e
 # DRAM traffic (read + write bytes) per launch of a kernel class on a workload,
 # from the committed ncu captures (profiles/); absent where no capture of the
 # current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH: dict[tuple[str, str], float] = {}
+NCU_TRAFFIC_PER_LAUNCH: dict[tuple[str, str], float] = {
+    # k_fgemm_limb<2, 1>, mean of the 833 launches of one 32768^2 factorization
+    # (profiles/fgemm_traffic_uniform32768_p65521.md)
+    ("uniform-32768-p65521", "fgemm"): 110.6e6,
+}
 
 
 def class_rooflines(classes: dict, peaks: dict) -> dict:

@@ -393,7 +393,8 @@ int pluq_autotune(pluq_ctx* ctx, uint32_t p, int64_t m, int64_t n, const uint32_
  * stream (0 stops recording; launches are counted either way).
  * pluq_profile_read(ctx, cls, ...) waits for the recorded events and returns,
  * for class cls (0 base-case tile, 1 fgemm tensor kernel, 2 operand packing,
- * 3 triangular diagonal blocks, 4 block gathers, 5 index vectors, 6 other),
+ * 3 triangular diagonal blocks, 4 block gathers, 5 index vectors, 6 other,
+ * 7 thin products on the CUDA cores),
  * the launch count, the summed device time in ms, the summed algorithmic
  * field operations (2 M N K for an fgemm) and bytes, and the summed tensor-pipe
  * flops actually issued (digit products included) of the timed launches.

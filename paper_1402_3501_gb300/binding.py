@@ -161,7 +161,7 @@ class Context:
     def set_tuning(self, bm: int = 0, bn: int = 0, trsm_block: int = 0):
         _check(load().pluq_set_tuning(self.handle, bm, bn, trsm_block), "pluq_set_tuning")
 
-    PROFILE_CLASSES = ["base", "fgemm", "pack", "trsm", "perm", "index", "other"]
+    PROFILE_CLASSES = ["base", "fgemm", "pack", "trsm", "perm", "index", "other", "thin"]
 
     def profile(self, enable: bool = True):
         """Reset the per-class launch counters; with enable, time every launch."""

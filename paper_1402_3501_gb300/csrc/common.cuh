@@ -121,6 +121,7 @@ enum ProfClass {
   PC_PERM,      // row / column block gathers and copy-back
   PC_INDEX,     // index-vector kernels (iota, compose, shifts)
   PC_OTHER,     // range check, copies, profiles, RREF scatter
+  PC_THIN,      // thin products on the CUDA cores
   PC_COUNT
 };
 
@@ -142,7 +143,7 @@ struct pluq_ctx {
   WsAccount ws_own;            // the user's context: its account
   WsAccount* ws = &ws_own;     // child contexts: the parent's account
   long long wait_cycles = 4000000000LL;  // bound of device waits (~2 s at 2 GHz)
-  int64_t launches[PC_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t launches[PC_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
   int device = 0;
   int sm_count = 0;
   cudaStream_t stream = nullptr;

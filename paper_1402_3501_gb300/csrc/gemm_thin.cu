@@ -91,7 +91,7 @@ int fgemm_sub_thin(pluq_ctx* c, int64_t M, int64_t N, int64_t K, const uint32_t*
                    const uint32_t* B, int64_t ldb, uint32_t* C, int64_t ldc) {
   if (M <= 0 || N <= 0 || K <= 0) return PLUQ_OK;
   if (cdiv(M, kThinTile) > 65535) return PLUQ_ERR_INVALID_ARG;
-  ProfScope ps(c, PC_FGEMM, 2.0 * M * N * K, 4.0 * (M * K + K * N + 2 * M * N), 1, 0.0);
+  ProfScope ps(c, PC_THIN, 2.0 * M * N * K, 4.0 * (M * K + K * N + 2 * M * N), 1, 0.0);
   const dim3 grid((unsigned)cdiv(N, kThinTile), (unsigned)cdiv(M, kThinTile));
   k_fgemm_thin<<<grid, kThinThreads, 0, c->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, c->F);
   PLUQ_CUDA(cudaGetLastError());
