@@ -42,8 +42,8 @@ METRIC = "PLUQ mod p effective Gfops (2n³/3/s), tensor-limb vs FP64 form, bit-e
 # current kernel exists.
 NCU_TRAFFIC_PER_LAUNCH: dict[tuple[str, str], float] = {
     # k_fgemm_limb<2, 1>, mean of the 833 launches of one 32768^2 factorization
-    # (profiles/fgemm_traffic_uniform32768_p65521.md)
-    ("uniform-32768-p65521", "fgemm"): 110.6e6,
+    # (profiles/launch_list_uniform32768_p65521.md, second capture)
+    ("uniform-32768-p65521", "fgemm"): 108.6e6,
 }
 
 

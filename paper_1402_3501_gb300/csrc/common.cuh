@@ -179,6 +179,7 @@ struct pluq_ctx {
   cudaGraphExec_t batch_graph = nullptr;  // captured batched launch
   int batch_graph_count = -1;
   int64_t batch_graph_elems = 0;
+  int batch_graph_maxn = 0;          // widest matrix the captured launch was sized for
   uint32_t batch_graph_p = 0;        // field and inverse table baked into the graph
   const void* batch_graph_tab = nullptr;
   DevBuf batch_scratch;    // per-CTA gather scratch of the batched kernel
@@ -272,9 +273,9 @@ int tile_leaf_fits(pluq_ctx* c, int64_t m, int64_t n);
 int leaf_max_dim();
 int launch_iota(pluq_ctx* c, int32_t* dst, int64_t count);
 int batched_max_dim();
-int batched_ctas_per_sm();
+int batched_grid(pluq_ctx* c, int max_n);
 int launch_batched(pluq_ctx* c, const void* descs, const int32_t* order, int count,
-                   int64_t* ranks, int32_t* status, int max_elems);
+                   int64_t* ranks, int32_t* status, int max_elems, int max_n);
 size_t batched_desc_size();
 void batched_fill_desc(void* out, int i, uint32_t* A, int32_t* P, int32_t* Q, int64_t lda, int m,
                        int n);

@@ -1180,17 +1180,19 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
     PLUQ_TRY(c->batch_dev.ensure(total));
     char* hb = static_cast<char*>(c->batch_host);
     char* db = c->batch_dev.as<char>();
-    int max_elems = 1;
+    int max_elems = 1, max_n = 1;
     for (int i = 0; i < cnt; ++i) {
       const int b = small[i];
       batched_fill_desc(hb, i, A[b], P[b], Q[b], lda[b], (int)m[b], (int)n[b]);
       max_elems = std::max<int64_t>(max_elems, m[b] * n[b]);
+      max_n = std::max<int64_t>(max_n, n[b]);
     }
     std::memcpy(hb + off_order, order.data(), sizeof(int32_t) * cnt);
     // one graph per (count, workspace): H2D descriptors, persistent kernel,
     // D2H ranks and status
     if (c->batch_graph && (c->batch_graph_count != cnt || c->batch_graph_key != db ||
                            old_dev != c->batch_dev.ptr || c->batch_graph_elems < max_elems ||
+                           c->batch_graph_maxn != max_n ||
                            c->batch_graph_p != c->F.p ||
                            c->batch_graph_tab != (const void*)inv_table_ptr(c))) {
       cudaGraphExecDestroy(c->batch_graph);
@@ -1198,8 +1200,9 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
     }
     if (!c->batch_graph) {
       // the gather scratch is sized (and captured) for this batch's largest matrix
-      PLUQ_TRY(c->batch_scratch.ensure(sizeof(uint32_t) * (size_t)max_elems * c->sm_count *
-                                       batched_ctas_per_sm()));
+      const int grid = batched_grid(c, max_n);
+      if (grid <= 0) return PLUQ_ERR_CUDA;
+      PLUQ_TRY(c->batch_scratch.ensure(sizeof(uint32_t) * (size_t)max_elems * grid));
       cudaStream_t cs;
       PLUQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
       cudaStream_t saved = c->stream;
@@ -1214,7 +1217,7 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
         if (st == PLUQ_OK)
           st = launch_batched(c, db, reinterpret_cast<const int32_t*>(db + off_order), cnt,
                               reinterpret_cast<int64_t*>(db + off_rank),
-                              reinterpret_cast<int32_t*>(db + off_stat), max_elems);
+                              reinterpret_cast<int32_t*>(db + off_stat), max_elems, max_n);
         if (st == PLUQ_OK &&
             cudaMemcpyAsync(hb + off_rank, db + off_rank, off_stat - off_rank + sizeof(int32_t) * cnt,
                             cudaMemcpyDeviceToHost, cs) != cudaSuccess)
@@ -1234,6 +1237,7 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
       c->batch_graph_count = cnt;
       c->batch_graph_key = db;
       c->batch_graph_elems = max_elems;
+      c->batch_graph_maxn = max_n;
       c->batch_graph_p = c->F.p;
       c->batch_graph_tab = inv_table_ptr(c);
     }

@@ -741,12 +741,18 @@ def _batch_cases(p, seed):
         cases.append(workloads.prescribed_rank_matrix(m, n, r, p, seed=int(rng.integers(1 << 30))).A)
     cases += [np.zeros((5, 7), np.uint32), np.eye(1, dtype=np.uint32), np.zeros((0, 4), np.uint32),
               workloads.uniform_matrix(1, 300, p, seed), workloads.uniform_matrix(300, 1, p, seed),
-              workloads.uniform_matrix(1024, 64, p, seed), workloads.uniform_matrix(1100, 40, p, seed)]
+              workloads.uniform_matrix(1024, 64, p, seed), workloads.uniform_matrix(1100, 40, p, seed),
+              workloads.uniform_matrix(1000, 1024, p, seed),
+              workloads.prescribed_rank_matrix(700, 900, 333, p, seed=seed).A]
     return cases
 
 
-@pytest.mark.parametrize("p", [2, 65521, 131071])
+@pytest.mark.parametrize("p", [2, 65521, 131071, 134217757, 2147483647])
 def test_batched_parity(ctx, p):
+    """Every matrix of a mixed batch (empty, one-row, one-column, rank-deficient,
+    the widest the persistent kernel takes, one past it) against the oracle, for
+    each of the slab kernel's field modes: p = 2, p < 2^27 (one reduction per dot
+    product) and larger p (a reduction per product)."""
     cases = _batch_cases(p, 3)
     As = [to_dev(A) for A in cases]
     for rep in range(2):  # the second call replays the captured graph
