@@ -8,25 +8,34 @@
 // complement, so the rows are taken in order and each row, once reduced by all
 // earlier pivots, is either zero or gives a pivot at its first non-zero column.
 //
-// The elimination is blocked by row slabs of kSlab rows, the tiled iterative
-// scheme of Sec. 4.1 with one column tile:
-//   1. the slab (reduced by every earlier slab) is loaded into shared memory
-//      with the earlier pivot columns zeroed, and eliminated row by row there
-//      (pivot search, rank-1 updates of the slab rows below the pivot row);
-//   2. the slab goes back to the matrix: multipliers at its pivot columns,
-//      reduced rows elsewhere; earlier pivot columns keep the multipliers the
-//      earlier slabs wrote;
-//   3. the rows below are reduced by the slab's nb pivots at once: their
-//      multipliers L = X U_JJ^{-1} (X: their entries at the slab's pivot
-//      columns, U_JJ: the pivot rows at those columns, upper triangular in
-//      pivot order) by a forward substitution per row, then C <- C - L U in
-//      64 x 64 tiles of 4 x 4 register micro-tiles, the nb products of every
-//      output summed in 64 bits and reduced once (delayed reduction, Sec. 3.1).
-// The pivot rows are kept in Montgomery form (x R mod p, R = 2^32) for step 3,
-// so the reduction of a sum of products L * (U R) is one REDC.  L multipliers
-// overwrite the pivot column entries; the final P^T A Q^T layout is gathered
-// through the CTA's scratch and copied back.  Entries >= p mark the matrix with
-// PLUQ_ERR_ENTRY_OUT_OF_RANGE and leave it untouched.
+// The elimination is the tiled iterative scheme of Sec. 4.1 with one column
+// tile, its row slabs cut by pivot count rather than by row count, so that every
+// update of the rows below carries many pivots.  A slab collects pivots in a
+// shared-memory buffer of kSlab rows (pivot rows at the top, candidate rows
+// below), in rounds:
+//   1. the next rows of the matrix fill the free buffer rows (the pivot columns
+//      of earlier slabs zeroed);
+//   2. they are reduced by the slab's pivots so far: multipliers by forward
+//      substitution on the pivot columns, then rows -= L U with the products of
+//      every entry summed in 64 bits and reduced once (delayed reduction,
+//      Sec. 3.1);
+//   3. they are eliminated among themselves in row order (pivot search, rank-1
+//      updates spread over all warps as (row, 32-column) items);
+//   4. the rows that gave no pivot are final and go back to the matrix; the new
+//      pivot rows move up.
+// The slab closes once fewer than kMinFree buffer rows are free (or the matrix
+// ends): its pivot rows go back to the matrix and the rows below are reduced by
+// its pivots at once, L from a forward substitution per row, then C <- C - L U
+// in 64 x 64 tiles of 4 x 4 register micro-tiles.  Multipliers are kept in
+// Montgomery form (x R mod p, R = 2^32) as left operands, so the reduction of
+// a sum of products (L R) * U is one REDC.  L multipliers overwrite the pivot
+// column entries.
+//
+// The final P^T A Q^T layout is written in place: the multipliers of the
+// non-pivot rows are first copied to the CTA's scratch, the pivot rows are then
+// moved up eight at a time through shared memory (a pivot row never moves down),
+// and the non-pivot rows are written from the scratch.  Entries >= p mark the
+// matrix with PLUQ_ERR_ENTRY_OUT_OF_RANGE and leave it untouched.
 #include <algorithm>
 #include <climits>
 #include <numeric>
@@ -39,9 +48,13 @@ namespace {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchMax = 1024;
-constexpr int kSlab = 32;  // rows eliminated in shared memory together
+constexpr int kSlab = 32;       // rows of the shared-memory buffer; most pivots of a slab
+constexpr int kMinFree = 8;     // a slab closes when fewer buffer rows than this are free
 constexpr int kRowBlock = 128;  // rows below the slab whose multipliers are formed together
-constexpr int kTile = 64;       // C tile of the update, 4 x 4 per thread
+constexpr int kTile = 64;       // C tile of the update below the slab, 4 x 4 per thread
+constexpr int kLd = 128;        // buffer rows are padded to a multiple of this many words
+constexpr int kLoadBatch = 8;   // global loads a lane keeps in flight
+constexpr int kItemUnroll = 4;  // (row, chunk) items a warp updates together
 
 struct BatchDesc {
   uint32_t* A;
@@ -65,20 +78,24 @@ struct BField {
     if (kMode == 0) return v & 1u;
     return f_redc((uint64_t)v * F.r2, F);
   }
+  __device__ __forceinline__ static uint32_t from_mont(uint32_t v, const FieldP& F) {
+    if (kMode == 0) return v;
+    return f_redc((uint64_t)v, F);
+  }
 };
 
-// sum of plain a times Montgomery b over a dot product, as a plain residue
+// sum of Montgomery a times plain b over a dot product, as a plain residue
 template <int kMode>
 struct Dot {
   uint64_t acc = 0;
   uint32_t red = 0;
-  __device__ __forceinline__ void add(uint32_t a, uint32_t bm, const FieldP& F) {
+  __device__ __forceinline__ void add(uint32_t am, uint32_t b, const FieldP& F) {
     if (kMode == 0) {
-      red ^= a & bm;
+      red ^= am & b;
     } else if (kMode == 1) {
-      acc += (uint64_t)a * bm;
+      acc += (uint64_t)am * b;
     } else {
-      red = f_add(red, f_redc((uint64_t)a * bm, F), F);
+      red = f_add(red, f_redc((uint64_t)am * b, F), F);
     }
   }
   __device__ __forceinline__ uint32_t value(const FieldP& F) const {
@@ -128,14 +145,33 @@ __device__ void bt_compact(const int32_t* flag, int cnt, int32_t* out, int base,
   __syncthreads();
 }
 
-// Shared memory of one CTA, in 32-bit words, for rows of ldS words.
+// n words of row src (global) into dst (shared), zero where drop(j), zero
+// from n to ld; kLoadBatch loads of a lane in flight.  One warp.
+template <typename Drop>
+__device__ __forceinline__ void bt_load_row(uint32_t* dst, const uint32_t* src, int n, int ld,
+                                            Drop drop) {
+  const int lane = threadIdx.x & 31;
+  for (int jb0 = 0; jb0 < ld; jb0 += 32 * kLoadBatch) {
+    uint32_t v[kLoadBatch];
+#pragma unroll
+    for (int q = 0; q < kLoadBatch; ++q) {
+      const int j = jb0 + 32 * q + lane;
+      v[q] = (j < n && !drop(j)) ? src[j] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kLoadBatch; ++q) {
+      const int j = jb0 + 32 * q + lane;
+      if (j < ld) dst[j] = v[q];
+    }
+  }
+}
+
+// Shared memory of one CTA, in 32-bit words, for buffer rows of ldS words.
 __host__ __device__ constexpr size_t slab_smem_words(int ldS) {
-  return (size_t)kSlab * ldS              // S: the slab, then the pivot rows (Montgomery)
-         + (size_t)kSlab * kRowBlock      // LT: multipliers of a row block, pivot-major
-         + (size_t)kSlab * kSlab          // Ls: multipliers inside the slab
-         + (size_t)kSlab * (kSlab + 1)    // Ujj: pivot rows at the pivot columns (Montgomery)
-         + kSlab                          // invm: inverse pivots (Montgomery)
-         + 3 * kSlab                      // first, spr, spc
+  return (size_t)kSlab * ldS              // S: pivot rows, then candidate rows (plain)
+         + (size_t)kSlab * kRowBlock      // LT: multipliers of a row block, pivot-major (Montgomery)
+         + (size_t)kSlab * kSlab          // Ls: multipliers of the buffer rows (plain)
+         + 8 * kSlab                      // spr, spc, invm, first, srow, lrow, lmrow, pslot
          + (size_t)ldS                    // ispiv
          + 2 * (size_t)kBatchMax          // prow, pcol
          + kBatchWarps + 8;               // red, misc
@@ -153,22 +189,24 @@ __global__ void __launch_bounds__(kBatchThreads)
   uint32_t* S = smem;
   uint32_t* LT = S + (size_t)kSlab * ldS;
   uint32_t* Ls = LT + kSlab * kRowBlock;
-  uint32_t* Ujj = Ls + kSlab * kSlab;
-  uint32_t* invm = Ujj + kSlab * (kSlab + 1);
-  int32_t* first = reinterpret_cast<int32_t*>(invm + kSlab);
-  int32_t* spr = first + kSlab;
-  int32_t* spc = spr + kSlab;
-  int32_t* ispiv = spc + kSlab;  // 0: not a pivot column; else 1 + its pivot index
+  int32_t* spr = reinterpret_cast<int32_t*>(Ls + kSlab * kSlab);  // slab pivot -> matrix row
+  int32_t* spc = spr + kSlab;                                      // slab pivot -> column
+  uint32_t* invm = reinterpret_cast<uint32_t*>(spc + kSlab);       // inverse pivot (Montgomery)
+  int32_t* first = reinterpret_cast<int32_t*>(invm + kSlab);       // buffer row -> first non-zero
+  int32_t* srow = first + kSlab;                                   // buffer row -> matrix row
+  uint32_t* lrow = reinterpret_cast<uint32_t*>(srow + kSlab);      // multipliers of one step
+  uint32_t* lmrow = lrow + kSlab;
+  int32_t* pslot = reinterpret_cast<int32_t*>(lmrow + kSlab);      // a round's pivots' buffer rows
+  int32_t* ispiv = pslot + kSlab;  // 0: not a pivot column; else 1 + its pivot index
   int32_t* prow = ispiv + ldS;
   int32_t* pcol = prow + kBatchMax;
   int* red = pcol + kBatchMax;
   int* s_idx = red + kBatchWarps;
-  // the final gather's index arrays reuse the slab and multiplier space
-  int32_t* isprow = reinterpret_cast<int32_t*>(S);
-  int32_t* rowpos = isprow + kBatchMax;
+  // the final layout's index arrays reuse the multiplier space
+  int32_t* isprow = reinterpret_cast<int32_t*>(Ls);  // kSlab * kSlab = kBatchMax words
+  int32_t* rowpos = reinterpret_cast<int32_t*>(LT);  // kSlab * kRowBlock >= 2 kBatchMax words
   int32_t* colpos = rowpos + kBatchMax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tx = tid & 15, ty = tid >> 4;
   uint32_t* SC = scratch + (size_t)blockIdx.x * scratch_per_cta;
 
   while (true) {
@@ -193,8 +231,19 @@ __global__ void __launch_bounds__(kBatchThreads)
     }
     // entries must be residues
     int bad = 0;
-    for (int l = warp; l < m; l += kBatchWarps)
-      for (int j = lane; j < n; j += 32) bad |= A[(int64_t)l * lda + j] >= F.p;
+    for (int l = warp; l < m; l += kBatchWarps) {
+      const uint32_t* row = A + (int64_t)l * lda;
+      for (int jb0 = 0; jb0 < n; jb0 += 32 * kLoadBatch) {
+        uint32_t v[kLoadBatch];
+#pragma unroll
+        for (int q = 0; q < kLoadBatch; ++q) {
+          const int j = jb0 + 32 * q + lane;
+          v[q] = j < n ? row[j] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kLoadBatch; ++q) bad |= v[q] >= F.p;
+      }
+    }
     if (bt_block_or(bad, red)) {
       if (tid == 0) {
         ranks[b] = -1;
@@ -204,111 +253,217 @@ __global__ void __launch_bounds__(kBatchThreads)
     }
     for (int j = tid; j < ldS; j += kBatchThreads) ispiv[j] = 0;
     __syncthreads();
-    int r = 0;
-    for (int i0 = 0; i0 < m; i0 += kSlab) {
-      const int bh = min(kSlab, m - i0);
-      // 1. the slab, earlier pivot columns and columns >= n zeroed; first non-zeros
-      for (int t = warp; t < kSlab; t += kBatchWarps) {
-        const uint32_t* row = A + (int64_t)(i0 + t) * lda;
-        uint32_t* st = S + (size_t)t * ldS;
-        int fz = INT_MAX;
-        for (int jb = 0; jb < ldS; jb += 32) {
-          const int j = jb + lane;
-          const uint32_t v = (t < bh && j < n && ispiv[j] == 0) ? row[j] : 0u;
-          st[j] = v;
-          const unsigned nz = __ballot_sync(0xffffffffu, v != 0u);
-          if (nz && fz == INT_MAX) fz = jb + __ffs(nz) - 1;
+    int r = 0, next = 0;
+    while (next < m) {
+      int P = 0;  // pivots of this slab so far, in buffer rows 0..P-1
+      while (true) {
+        const int c = min(kSlab - P, m - next);  // rows taken in this round
+        // 1. rows next.. into buffer rows P..P+c-1, earlier slabs' pivot columns zeroed
+        for (int i = warp; i < c; i += kBatchWarps) {
+          const int s = P + i;
+          bt_load_row(S + (size_t)s * ldS, A + (int64_t)(next + i) * lda, n, ldS, [&](int j) {
+            const int f = ispiv[j];
+            return f != 0 && f <= r;
+          });
+          Ls[s * kSlab + lane] = 0u;
+          if (lane == 0) srow[s] = next + i;
         }
-        if (lane == 0) first[t] = fz;
-        Ls[t * kSlab + lane] = 0u;
-      }
-      __syncthreads();
-      int nb = 0;
-      for (int t = 0; t < bh; ++t) {
-        const int js = first[t];
-        if (js == INT_MAX) continue;  // row t of the slab is zero: no pivot
-        const uint32_t* pr = S + (size_t)t * ldS;
-        const uint32_t inv = f_inv(pr[js], F, inv_table);
-        const uint32_t im = BF::to_mont(inv, F);
-        for (int u = t + 1 + warp; u < bh; u += kBatchWarps) {
-          uint32_t* ur = S + (size_t)u * ldS;
-          const uint32_t w = ur[js];
-          if (w == 0u) continue;  // unchanged; its first non-zero is not js
-          const uint32_t l = BF::mulm(im, w, F);
-          const uint32_t lm = BF::to_mont(l, F);
+        __syncthreads();
+        if (P > 0) {
+          // 2. their multipliers for the slab's pivots (forward substitution on the
+          // pivot columns, a thread a row) ...
+          if (tid < c) {
+            const uint32_t* st = S + (size_t)(P + tid) * ldS;
+            for (int k = 0; k < P; ++k) {
+              const int jk = spc[k];
+              Dot<kMode> s;
+              for (int q = 0; q < k; ++q) s.add(LT[q * kRowBlock + tid], S[(size_t)q * ldS + jk], F);
+              const uint32_t l = BF::mulm(invm[k], f_sub(st[jk], s.value(F), F), F);
+              Ls[(P + tid) * kSlab + k] = l;
+              LT[k * kRowBlock + tid] = BF::to_mont(l, F);
+            }
+          } else if (tid < kSlab) {
+            for (int k = 0; k < P; ++k) LT[k * kRowBlock + tid] = 0u;
+          }
+          __syncthreads();
+          // ... then rows -= L U over every column: warp w takes rows 4w..4w+3,
+          // lane l columns c0 + l + 32 jj
+          const int rt = warp * 4;
+          for (int c0 = 0; c0 < n; c0 += 128) {
+            Dot<kMode> acc[4][4];
+#pragma unroll 2
+            for (int k = 0; k < P; ++k) {
+              const uint4 a4 = *reinterpret_cast<const uint4*>(LT + k * kRowBlock + rt);
+              const uint32_t a[4] = {a4.x, a4.y, a4.z, a4.w};
+              uint32_t bv[4];
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) bv[jj] = S[(size_t)k * ldS + c0 + lane + 32 * jj];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj].add(a[i], bv[jj], F);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) {
+                const int row = rt + i, col = c0 + lane + 32 * jj;
+                if (row < c && col < n) {
+                  uint32_t* e = S + (size_t)(P + row) * ldS + col;
+                  *e = f_sub(*e, acc[i][jj].value(F), F);
+                }
+              }
+          }
+          __syncthreads();
+        }
+        // first non-zero of each new row
+        for (int i = warp; i < c; i += kBatchWarps) {
+          const uint32_t* st = S + (size_t)(P + i) * ldS;
           int fz = INT_MAX;
           for (int jb = 0; jb < n; jb += 32) {
-            const int j = jb + lane;
-            uint32_t nv = 0u;
-            if (j < n) {
-              nv = f_sub(ur[j], BF::mulm(lm, pr[j], F), F);
-              ur[j] = nv;
+            const unsigned nz = __ballot_sync(0xffffffffu, jb + lane < n && st[jb + lane] != 0u);
+            if (nz) {
+              fz = jb + __ffs(nz) - 1;
+              break;
             }
-            const unsigned nz = __ballot_sync(0xffffffffu, nv != 0u);
-            if (nz && fz == INT_MAX) fz = jb + __ffs(nz) - 1;
           }
-          if (lane == 0) {
-            Ls[u * kSlab + nb] = l;
-            first[u] = fz;
-          }
+          if (lane == 0) first[P + i] = fz;
         }
-        if (tid == 0) {
-          spr[nb] = t;
-          spc[nb] = js;
-          invm[nb] = im;
-        }
-        ++nb;
         __syncthreads();
+        // 3. the new rows among themselves, in row order
+        int np = 0;
+        const int nch = (n + 31) >> 5;
+        for (int s = P; s < P + c; ++s) {
+          const int js = first[s];
+          if (js == INT_MAX) continue;  // a zero row: no pivot
+          const int k = P + np;
+          const uint32_t* pr = S + (size_t)s * ldS;
+          const int ub = s + 1, ue = P + c;
+          if (warp == 0) {
+            const uint32_t im = BF::to_mont(f_inv(pr[js], F, inv_table), F);
+            const int u = ub + lane;
+            if (u < ue) {
+              const uint32_t w = S[(size_t)u * ldS + js];
+              const uint32_t l = w != 0u ? BF::mulm(im, w, F) : 0u;
+              lrow[u] = l;
+              lmrow[u] = BF::to_mont(l, F);
+              Ls[u * kSlab + k] = l;
+              if (w != 0u) first[u] = INT_MAX;
+            }
+            if (lane == 0) {
+              spr[k] = srow[s];
+              spc[k] = js;
+              invm[k] = im;
+              pslot[np] = s;
+              ispiv[js] = r + k + 1;
+            }
+          }
+          ++np;
+          __syncthreads();
+          // rank-1 update of the rows below it, as (row, 32-column chunk) items
+          const int items = (ue - ub) * nch;
+          for (int it0 = warp * kItemUnroll; it0 < items; it0 += kBatchWarps * kItemUnroll) {
+            uint32_t nv[kItemUnroll];
+            int iu[kItemUnroll], jb[kItemUnroll];
+            bool act[kItemUnroll];
+#pragma unroll
+            for (int q = 0; q < kItemUnroll; ++q) {
+              const int it = it0 + q;
+              const int du = it / nch;
+              iu[q] = ub + du;
+              jb[q] = (it - du * nch) * 32;
+              const uint32_t lm = it < items ? lmrow[iu[q]] : 0u;
+              act[q] = lm != 0u;
+              const int j = jb[q] + lane;
+              nv[q] = (act[q] && j < n)
+                          ? f_sub(S[(size_t)iu[q] * ldS + j], BF::mulm(lm, pr[j], F), F)
+                          : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < kItemUnroll; ++q) {
+              if (!act[q]) continue;  // warp-uniform
+              const int j = jb[q] + lane;
+              if (j < n) S[(size_t)iu[q] * ldS + j] = nv[q];
+              const unsigned nz = __ballot_sync(0xffffffffu, nv[q] != 0u);
+              if (nz && lane == 0) atomicMin(first + iu[q], jb[q] + __ffs(nz) - 1);
+            }
+          }
+          __syncthreads();
+        }
+        // 4. rows without a pivot are final: back to the matrix (the multipliers
+        // of this slab at its pivot columns, zero elsewhere; earlier slabs'
+        // pivot columns keep their multipliers)
+        for (int s = P + warp; s < P + c; s += kBatchWarps) {
+          if (first[s] != INT_MAX) continue;
+          uint32_t* row = A + (int64_t)srow[s] * lda;
+          for (int j = lane; j < n; j += 32) {
+            const int f = ispiv[j];
+            if (f != 0 && f <= r) continue;
+            row[j] = f > r ? Ls[s * kSlab + (f - r - 1)] : 0u;
+          }
+        }
+        __syncthreads();
+        // the round's pivot rows move up to buffer rows P..P+np-1 (pslot[i] >=
+        // P + i, increasing: each column moved in increasing i)
+        for (int j = tid; j < ldS; j += kBatchThreads)
+          for (int i = 0; i < np; ++i)
+            if (pslot[i] != P + i) S[(size_t)(P + i) * ldS + j] = S[(size_t)pslot[i] * ldS + j];
+        if (tid < kSlab)
+          for (int i = 0; i < np; ++i)
+            if (pslot[i] != P + i) Ls[(P + i) * kSlab + tid] = Ls[pslot[i] * kSlab + tid];
+        __syncthreads();
+        P += np;
+        next += c;
+        if (P > kSlab - kMinFree || next >= m) break;
       }
-      for (int k = tid; k < nb; k += kBatchThreads) {
-        prow[r + k] = i0 + spr[k];
-        pcol[r + k] = spc[k];
-        ispiv[spc[k]] = r + k + 1;
-      }
-      __syncthreads();
-      // 2. back to the matrix
-      for (int t = warp; t < bh; t += kBatchWarps) {
-        uint32_t* row = A + (int64_t)(i0 + t) * lda;
-        const uint32_t* st = S + (size_t)t * ldS;
+      // the slab's pivot rows back to the matrix: multipliers at the columns of
+      // the slab's earlier pivots, the reduced row elsewhere
+      for (int k = warp; k < P; k += kBatchWarps) {
+        uint32_t* row = A + (int64_t)spr[k] * lda;
+        const uint32_t* st = S + (size_t)k * ldS;
         for (int j = lane; j < n; j += 32) {
           const int f = ispiv[j];
-          if (f != 0 && f <= r) continue;  // an earlier pivot column: its multiplier stays
-          uint32_t v = st[j];
-          if (f > r && spr[f - r - 1] < t) v = Ls[t * kSlab + (f - r - 1)];
-          row[j] = v;
+          if (f != 0 && f <= r) continue;
+          const int kk = f - r - 1;
+          row[j] = (f > r && kk < k) ? Ls[k * kSlab + kk] : st[j];
         }
       }
+      for (int k = tid; k < P; k += kBatchThreads) {
+        prow[r + k] = spr[k];
+        pcol[r + k] = spc[k];
+      }
       __syncthreads();
-      if (nb > 0 && i0 + bh < m) {
-        // 3. pivot rows to rows 0..nb-1 of S in Montgomery form (spr[k] >= k, so
-        // each column is moved in place in increasing k)
-        for (int j = tid; j < ldS; j += kBatchThreads)
-          for (int k = 0; k < nb; ++k)
-            S[(size_t)k * ldS + j] = BF::to_mont(S[(size_t)spr[k] * ldS + j], F);
-        __syncthreads();
-        for (int e = tid; e < nb * nb; e += kBatchThreads) {
-          const int q = e / nb, k = e - q * nb;
-          Ujj[q * (kSlab + 1) + k] = S[(size_t)q * ldS + spc[k]];
-        }
-        __syncthreads();
-        for (int rb = i0 + bh; rb < m; rb += kRowBlock) {
+      // the rows below reduced by the slab's P pivots
+      if (P > 0 && next < m) {
+        for (int rb = next; rb < m; rb += kRowBlock) {
           const int nr = min(kRowBlock, m - rb);
           if (tid < kRowBlock) {
-            // multipliers of row rb + tid: L_k = (x_k - sum_{q<k} L_q U_q[j_k]) / U_k[j_k]
             if (tid < nr) {
+              // the row's entries at the pivot columns, then L by forward substitution
               const uint32_t* ar = A + (int64_t)(rb + tid) * lda;
-              for (int k = 0; k < nb; ++k) {
-                const uint32_t x = ar[spc[k]];
+              for (int k0 = 0; k0 < P; k0 += kLoadBatch) {
+                uint32_t x[kLoadBatch];
+#pragma unroll
+                for (int q = 0; q < kLoadBatch; ++q) x[q] = k0 + q < P ? ar[spc[k0 + q]] : 0u;
+#pragma unroll
+                for (int q = 0; q < kLoadBatch; ++q)
+                  if (k0 + q < P) LT[(k0 + q) * kRowBlock + tid] = x[q];
+              }
+              for (int k = 0; k < P; ++k) {
+                const int jk = spc[k];
                 Dot<kMode> s;
-                for (int q = 0; q < k; ++q) s.add(LT[q * kRowBlock + tid], Ujj[q * (kSlab + 1) + k], F);
-                LT[k * kRowBlock + tid] = BF::mulm(invm[k], f_sub(x, s.value(F), F), F);
+                for (int q = 0; q < k; ++q) s.add(LT[q * kRowBlock + tid], S[(size_t)q * ldS + jk], F);
+                const uint32_t l =
+                    BF::mulm(invm[k], f_sub(LT[k * kRowBlock + tid], s.value(F), F), F);
+                LT[k * kRowBlock + tid] = BF::to_mont(l, F);
               }
             } else {
-              for (int k = 0; k < nb; ++k) LT[k * kRowBlock + tid] = 0u;
+              for (int k = 0; k < P; ++k) LT[k * kRowBlock + tid] = 0u;
             }
           }
           __syncthreads();
           // C <- C - L U; the slab's pivot columns take L
+          const int tx = tid & 15, ty = tid >> 4;
           for (int sub = 0; sub < nr; sub += kTile) {
             const int rl = sub + ty * 4;  // first of this thread's rows within the block
             for (int c0 = 0; c0 < n; c0 += kTile) {
@@ -322,7 +477,7 @@ __global__ void __launch_bounds__(kBatchThreads)
                 }
               Dot<kMode> acc[4][4];
 #pragma unroll 2
-              for (int k = 0; k < nb; ++k) {
+              for (int k = 0; k < P; ++k) {
                 const uint4 a4 = *reinterpret_cast<const uint4*>(LT + k * kRowBlock + rl);
                 const uint32_t a[4] = {a4.x, a4.y, a4.z, a4.w};
                 uint32_t bv[4];
@@ -340,7 +495,7 @@ __global__ void __launch_bounds__(kBatchThreads)
                   const int row = rl + i, col = c0 + tx + 16 * jj;
                   if (row < nr && col < n) {
                     const int f = ispiv[col];
-                    const uint32_t v = f > r ? LT[(f - r - 1) * kRowBlock + row]
+                    const uint32_t v = f > r ? BF::from_mont(LT[(f - r - 1) * kRowBlock + row], F)
                                              : f_sub(cv[i][jj], acc[i][jj].value(F), F);
                     A[(int64_t)(rb + row) * lda + col] = v;
                   }
@@ -350,9 +505,9 @@ __global__ void __launch_bounds__(kBatchThreads)
           __syncthreads();
         }
       }
-      r += nb;
+      r += P;
     }
-    // P = [pivot rows, others ascending], Q likewise; gather through scratch
+    // P = [pivot rows, others ascending], Q likewise
     for (int i = tid; i < m; i += kBatchThreads) isprow[i] = 0;
     for (int j = tid; j < n; j += kBatchThreads) ispiv[j] = 0;
     __syncthreads();
@@ -365,16 +520,31 @@ __global__ void __launch_bounds__(kBatchThreads)
     __syncthreads();
     bt_compact(isprow, m, rowpos, r, red);
     bt_compact(ispiv, n, colpos, r, red);
-    for (int t = warp; t < m; t += kBatchWarps) {
+    // the non-pivot rows' multipliers (at the pivot columns, in pivot order) to scratch
+    for (int t = r + warp; t < m; t += kBatchWarps) {
       const uint32_t* src = A + (int64_t)rowpos[t] * lda;
-      uint32_t* dst = SC + (size_t)t * n;
-      for (int u = lane; u < n; u += 32) dst[u] = (t >= r && u >= r) ? 0u : src[colpos[u]];
+      uint32_t* dst = SC + (size_t)(t - r) * r;
+      for (int u = lane; u < r; u += 32) dst[u] = src[colpos[u]];
     }
     __syncthreads();
-    for (int t = warp; t < m; t += kBatchWarps) {
-      const uint32_t* src = SC + (size_t)t * n;
+    // pivot rows up, eight at a time through shared memory: row t comes from
+    // rowpos[t] >= t, and rows below t0 + 8 are not read again
+    for (int t0 = 0; t0 < r; t0 += kBatchWarps) {
+      const int t = t0 + warp;
+      uint32_t* w = S + (size_t)warp * ldS;
+      if (t < r) bt_load_row(w, A + (int64_t)rowpos[t] * lda, n, ldS, [](int) { return false; });
+      __syncthreads();
+      if (t < r) {
+        uint32_t* dst = A + (int64_t)t * lda;
+        for (int u = lane; u < n; u += 32) dst[u] = w[colpos[u]];
+      }
+      __syncthreads();
+    }
+    // non-pivot rows: their multipliers, then zeros
+    for (int t = r + warp; t < m; t += kBatchWarps) {
+      const uint32_t* src = SC + (size_t)(t - r) * r;
       uint32_t* dst = A + (int64_t)t * lda;
-      for (int u = lane; u < n; u += 32) dst[u] = src[u];
+      for (int u = lane; u < n; u += 32) dst[u] = u < r ? src[u] : 0u;
     }
     for (int t = tid; t < m; t += kBatchThreads) d.P[t] = rowpos[t];
     for (int u = tid; u < n; u += kBatchThreads) d.Q[u] = colpos[u];
@@ -388,7 +558,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 
 __global__ void k_batch_reset(int* counter) { *counter = 0; }
 
-int slab_ld(int max_n) { return std::max(kTile, (int)cdiv(std::max(max_n, 1), kTile) * kTile); }
+int slab_ld(int max_n) { return (int)cdiv(std::max(max_n, 1), kLd) * kLd; }
 
 size_t slab_smem_bytes(int max_n) { return sizeof(uint32_t) * slab_smem_words(slab_ld(max_n)); }
 
