@@ -337,6 +337,11 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        none.  A call whose workspace would exceed the cap
  *                        returns PLUQ_ERR_NO_WORKSPACE; buffers already held
  *                        stay allocated until the context is destroyed.
+ *   PLUQ_OPT_BATCH_SLAB  0 (default), 16, 24 or 32: rows of the shared-memory
+ *                        buffer in which the batched factorization collects a
+ *                        slab's pivots (the most pivots one update of the rows
+ *                        below carries); smaller buffers fit more CTAs an SM.
+ *                        0: 16.
  * Errors: INVALID_ARG for an unknown option or a value out of range. */
 #define PLUQ_OPT_LEAF_DIM 1
 #define PLUQ_OPT_LEAF_KIND 2
@@ -356,6 +361,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_TRSM_STRIP 16
 #define PLUQ_OPT_FUSED_KMAX 17
 #define PLUQ_OPT_DIAG_INVERSES 18
+#define PLUQ_OPT_BATCH_SLAB 19
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

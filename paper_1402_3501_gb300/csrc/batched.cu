@@ -11,8 +11,9 @@
 // The elimination is the tiled iterative scheme of Sec. 4.1 with one column
 // tile, its row slabs cut by pivot count rather than by row count, so that every
 // update of the rows below carries many pivots.  A slab collects pivots in a
-// shared-memory buffer of kSlab rows (pivot rows at the top, candidate rows
-// below), in rounds:
+// shared-memory buffer of kSlab rows (16, 24 or 32: the template parameter that
+// trades pivots an update against CTAs an SM) -- pivot rows at the top,
+// candidate rows below -- in rounds:
 //   1. the next rows of the matrix fill the free buffer rows (the pivot columns
 //      of earlier slabs zeroed);
 //   2. they are reduced by the slab's pivots so far: multipliers by forward
@@ -20,10 +21,10 @@
 //      every entry summed in 64 bits and reduced once (delayed reduction,
 //      Sec. 3.1);
 //   3. they are eliminated among themselves in row order (pivot search, rank-1
-//      updates spread over all warps as (row, 32-column) items);
+//      updates of the rows below the pivot row, a warp a row);
 //   4. the rows that gave no pivot are final and go back to the matrix; the new
 //      pivot rows move up.
-// The slab closes once fewer than kMinFree buffer rows are free (or the matrix
+// The slab closes once fewer than kSlab / 4 buffer rows are free (or the matrix
 // ends): its pivot rows go back to the matrix and the rows below are reduced by
 // its pivots at once, L from a forward substitution per row, then C <- C - L U
 // in 64 x 64 tiles of 4 x 4 register micro-tiles.  Multipliers are kept in
@@ -48,13 +49,15 @@ namespace {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchMax = 1024;
-constexpr int kSlab = 32;       // rows of the shared-memory buffer; most pivots of a slab
-constexpr int kMinFree = 8;     // a slab closes when fewer buffer rows than this are free
 constexpr int kRowBlock = 128;  // rows below the slab whose multipliers are formed together
 constexpr int kTile = 64;       // C tile of the update below the slab, 4 x 4 per thread
-constexpr int kLd = 128;        // buffer rows are padded to a multiple of this many words
+constexpr int kLd = 256;        // buffer rows hold a multiple of this many columns ...
+constexpr int kPadS = 4;        // ... plus this many words, so that rows 2t and 2t + 1 (t < 4)
+                                // of a column fall in distinct banks
+constexpr int kLdL = kRowBlock + 4;  // row stride of the multipliers of a row block, likewise
+constexpr int kLdE = 36;             // row stride of U_JJ^{-1}, likewise
 constexpr int kLoadBatch = 8;   // global loads a lane keeps in flight
-constexpr int kItemUnroll = 4;  // (row, chunk) items a warp updates together
+constexpr int kRowUnroll = 8;   // 32-column chunks of a row a warp updates together
 
 struct BatchDesc {
   uint32_t* A;
@@ -67,7 +70,11 @@ struct BatchDesc {
 // Field arithmetic specialised by the size of p:
 //   0: p = 2 (bits);
 //   1: p < 2^27 (32 products of residues sum to less than p 2^32: one REDC);
-//   2: otherwise (a REDC per product).
+//   2: otherwise (a REDC per product);
+//   3: p < 2^16: as 1, and the update of the rows below runs on the tensor
+//      cores (residues split into two 8-bit digits, exact in FP16; see
+//      trailing_mma).
+__host__ __device__ constexpr bool one_redc(int mode) { return mode == 1 || mode == 3; }
 template <int kMode>
 struct BField {
   __device__ __forceinline__ static uint32_t mulm(uint32_t cm, uint32_t w, const FieldP& F) {
@@ -92,7 +99,7 @@ struct Dot {
   __device__ __forceinline__ void add(uint32_t am, uint32_t b, const FieldP& F) {
     if (kMode == 0) {
       red ^= am & b;
-    } else if (kMode == 1) {
+    } else if (one_redc(kMode)) {
       acc += (uint64_t)am * b;
     } else {
       red = f_add(red, f_redc((uint64_t)am * b, F), F);
@@ -100,10 +107,36 @@ struct Dot {
   }
   __device__ __forceinline__ uint32_t value(const FieldP& F) const {
     if (kMode == 0) return red & 1u;
-    if (kMode == 1) return f_redc(acc, F);
+    if (one_redc(kMode)) return f_redc(acc, F);
     return red;
   }
+  __device__ __forceinline__ void merge(const Dot& o, const FieldP& F) {
+    if (kMode == 0) red ^= o.red;
+    else if (one_redc(kMode)) acc += o.acc;
+    else red = f_add(red, o.red, F);
+  }
 };
+
+// sum_{q < k} a[q lda] b[q ldb] (a Montgomery, b plain) as a plain residue, in
+// four independent partial sums (k <= 32: the merged sum stays below p 2^32
+// in mode 1)
+template <int kMode>
+__device__ __forceinline__ uint32_t dot_prefix(const uint32_t* a, int lda, const uint32_t* b,
+                                               size_t ldb, int k, const FieldP& F) {
+  Dot<kMode> s0, s1, s2, s3;
+  int q = 0;
+  for (; q + 4 <= k; q += 4) {
+    s0.add(a[q * lda], b[q * ldb], F);
+    s1.add(a[(q + 1) * lda], b[(q + 1) * ldb], F);
+    s2.add(a[(q + 2) * lda], b[(q + 2) * ldb], F);
+    s3.add(a[(q + 3) * lda], b[(q + 3) * ldb], F);
+  }
+  for (; q < k; ++q) s0.add(a[q * lda], b[q * ldb], F);
+  s0.merge(s1, F);
+  s2.merge(s3, F);
+  s0.merge(s2, F);
+  return s0.value(F);
+}
 
 __device__ __forceinline__ int bt_block_or(int v, int* red) {
   v = __any_sync(0xffffffffu, v != 0) ? 1 : 0;
@@ -166,45 +199,184 @@ __device__ __forceinline__ void bt_load_row(uint32_t* dst, const uint32_t* src, 
   }
 }
 
-// Shared memory of one CTA, in 32-bit words, for buffer rows of ldS words.
-__host__ __device__ constexpr size_t slab_smem_words(int ldS) {
-  return (size_t)kSlab * ldS              // S: pivot rows, then candidate rows (plain)
-         + (size_t)kSlab * kRowBlock      // LT: multipliers of a row block, pivot-major (Montgomery)
+// Two 8-bit digits (v0 >> shift, v1 >> shift, low bytes) as an FP16 pair, exact:
+// 0x6400 | d is 1024 + d in FP16, and 1024 is subtracted.
+__device__ __forceinline__ uint32_t digit_pair(uint32_t v0, uint32_t v1, int shift) {
+  const uint32_t w = ((v0 >> shift) & 0xFFu) | (((v1 >> shift) & 0xFFu) << 16) | 0x64006400u;
+  uint32_t out;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(out) : "r"(w), "r"(0x64006400u));
+  return out;
+}
+
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
+  uint32_t out;
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(b));
+  return out;
+}
+
+// c += a b on a 16 x 8 x 16 tile (legacy warp-level tensor-core product; FP16
+// in, FP32 accumulate)
+__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// an FP32 holding an integer in [0, 2^23), as that integer
+__device__ __forceinline__ uint32_t f2u_exact(float x) {
+  return __float_as_uint(x + 8388608.0f) & 0x7FFFFFu;
+}
+
+// CTAs an SM the register budget is set for, by buffer height.
+__host__ __device__ constexpr int slab_min_blocks(int slab) { return slab >= 32 ? 2 : 3; }
+
+// Shared memory of one CTA, in 32-bit words, for buffer rows of ldN columns.
+template <int kSlab>
+__host__ __device__ constexpr size_t slab_smem_words(int ldN) {
+  return (size_t)kSlab * (ldN + kPadS)    // S: pivot rows, then candidate rows
+         + (size_t)kSlab * kLdL           // LT: multipliers (or entries) of a row block, pivot-major
+         + (size_t)kSlab * kLdE           // Uinv: U_JJ^{-1} of the tensor-core update
          + (size_t)kSlab * kSlab          // Ls: multipliers of the buffer rows (plain)
-         + 8 * kSlab                      // spr, spc, invm, first, srow, lrow, lmrow, pslot
-         + (size_t)ldS                    // ispiv
-         + 2 * (size_t)kBatchMax          // prow, pcol
+         + 6 * kSlab                      // spr, spc, invm, first, srow, pslot
+         + (size_t)ldN                    // ispiv
+         + (size_t)kBatchMax              // prow, pcol (16-bit)
          + kBatchWarps + 8;               // red, misc
 }
 
+
+// A block of nr <= kRowBlock rows below a slab, for p < 2^16, on the tensor
+// cores: with X the rows' entries at the slab's P <= 32 pivot columns (plain,
+// pivot-major in XT), W = U_JJ^{-1} U (P x n, Montgomery form, in S) and
+// U_JJ^{-1} (P x P, Montgomery form, Uinv),
+//   C <- C - X W    at the other columns,
+//   L  = X U_JJ^{-1} at the pivot columns (the multipliers),
+// i.e. C <- C - L U.  Every residue is split into two 8-bit digits,
+// x = x1 2^8 + x0, exact in FP16; per 16-deep step three products are
+// accumulated in FP32: X0 W0, X1 W1 and (X0 + X1)(W0 + W1) (digit sums <= 510),
+// each a sum of at most 32 products below 2^18, so below 2^23 and exact.  The
+// middle term is K - X0W0 - X1W1 and the dot product
+// x = X1W1 2^16 + mid 2^8 + X0W0 < 32 p^2 is reduced by one REDC (W carries R).
+// Warp w takes rows 16w..16w+15 of the block (its A fragments stay in
+// registers) and sweeps the columns 16 at a time, then the P columns of
+// U_JJ^{-1}.
 template <int kMode>
-__global__ void __launch_bounds__(kBatchThreads)
+__device__ __forceinline__ void trailing_mma(uint32_t* C, int64_t ldc, int nr, int n, int P,
+                                             const int32_t* spc, const uint32_t* XT,
+                                             const uint32_t* S, int ldS, const uint32_t* Uinv,
+                                             const int32_t* ispiv, int r, const FieldP& F) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int m0 = warp * 16;
+  if (m0 >= nr) return;
+  // A fragments: a[q] holds rows m0 + g (+8 for odd q), depth 2t, 2t + 1 (+8 for q >= 2)
+  uint32_t alo[2][4], ahi[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int row = m0 + g + ((q & 1) ? 8 : 0);
+      const int k0 = 16 * ks + 2 * t + ((q & 2) ? 8 : 0);
+      const uint32_t v0 = k0 < P ? XT[k0 * kLdL + row] : 0u;
+      const uint32_t v1 = k0 + 1 < P ? XT[(k0 + 1) * kLdL + row] : 0u;
+      alo[ks][q] = digit_pair(v0, v1, 0);
+      ahi[ks][q] = digit_pair(v0, v1, 8);
+    }
+  const bool two = P > 16;
+  const int ntiles = (n + 15) / 16, etiles = (P + 15) / 16;
+  for (int tile = 0; tile < ntiles + etiles; ++tile) {
+    const bool ext = tile >= ntiles;
+    const int c0 = ext ? 16 * (tile - ntiles) : 16 * tile;
+    // C entries of this lane: rows m0 + g (+8), columns c0 + 8 nt + 2t (+1)
+    uint32_t cv[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = m0 + g + (i >= 2 ? 8 : 0), col = c0 + 8 * nt + 2 * t + (i & 1);
+        cv[nt][i] = (!ext && row < nr && col < n) ? C[(int64_t)row * ldc + col] : 0u;
+      }
+    float acc[2][3][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[nt][d][i] = 0.0f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      if (ks == 1 && !two) break;
+      uint32_t asum[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) asum[q] = hadd2(alo[ks][q], ahi[ks][q]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int col = c0 + 8 * nt + g;
+        const int k0 = 16 * ks + 2 * t;
+        uint32_t u[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int k = k0 + (h & 1) + ((h & 2) ? 8 : 0);
+          u[h] = k < P ? (ext ? (col < P ? Uinv[k * kLdE + col] : 0u) : S[(size_t)k * ldS + col])
+                       : 0u;
+        }
+        const uint32_t bl0 = digit_pair(u[0], u[1], 0), bl1 = digit_pair(u[2], u[3], 0);
+        const uint32_t bh0 = digit_pair(u[0], u[1], 8), bh1 = digit_pair(u[2], u[3], 8);
+        mma16816(acc[nt][0], alo[ks], bl0, bl1);
+        mma16816(acc[nt][1], ahi[ks], bh0, bh1);
+        mma16816(acc[nt][2], asum, hadd2(bl0, bh0), hadd2(bl1, bh1));
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = m0 + g + (i >= 2 ? 8 : 0), col = c0 + 8 * nt + 2 * t + (i & 1);
+        if (row >= nr || col >= (ext ? P : n)) continue;
+        const uint32_t ll = f2u_exact(acc[nt][0][i]), hh = f2u_exact(acc[nt][1][i]);
+        const uint32_t mid = f2u_exact(acc[nt][2][i]) - ll - hh;
+        const uint32_t red = f_redc(((uint64_t)hh << 16) + (uint64_t)((mid << 8) + ll), F);
+        if (ext) {
+          C[(int64_t)row * ldc + spc[col]] = red;  // the multiplier of pivot col
+        } else if (ispiv[col] <= r) {            // not one of the slab's pivot columns
+          C[(int64_t)row * ldc + col] = f_sub(cv[nt][i], red, F);
+        }
+      }
+  }
+}
+
+template <int kMode, int kSlab>
+__global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
     k_batched_pluq(const BatchDesc* __restrict__ descs, const int32_t* __restrict__ order,
                    int batch, int* __restrict__ counter, FieldP F,
                    const uint32_t* __restrict__ inv_table, uint32_t* __restrict__ scratch,
-                   size_t scratch_per_cta, int ldS, int64_t* __restrict__ ranks,
+                   size_t scratch_per_cta, int ldN, int64_t* __restrict__ ranks,
                    int32_t* __restrict__ status) {
   using BF = BField<kMode>;
+  constexpr int kMinFree = kSlab / 4;  // a slab closes when fewer buffer rows are free
+  constexpr int kRG = kSlab <= 16 ? 4 : 8;   // row groups of 4 in the refill update
+  constexpr int kCL = kBatchThreads / kRG;   // column lanes: the update's tile is 4 kCL wide
   extern __shared__ __align__(16) uint32_t smem[];
+  const int ldS = ldN + kPadS;  // row stride of the buffer
   uint32_t* S = smem;
   uint32_t* LT = S + (size_t)kSlab * ldS;
-  uint32_t* Ls = LT + kSlab * kRowBlock;
+  uint32_t* Uinv = LT + kSlab * kLdL;
+  uint32_t* Ls = Uinv + kSlab * kLdE;
   int32_t* spr = reinterpret_cast<int32_t*>(Ls + kSlab * kSlab);  // slab pivot -> matrix row
   int32_t* spc = spr + kSlab;                                      // slab pivot -> column
   uint32_t* invm = reinterpret_cast<uint32_t*>(spc + kSlab);       // inverse pivot (Montgomery)
   int32_t* first = reinterpret_cast<int32_t*>(invm + kSlab);       // buffer row -> first non-zero
   int32_t* srow = first + kSlab;                                   // buffer row -> matrix row
-  uint32_t* lrow = reinterpret_cast<uint32_t*>(srow + kSlab);      // multipliers of one step
-  uint32_t* lmrow = lrow + kSlab;
-  int32_t* pslot = reinterpret_cast<int32_t*>(lmrow + kSlab);      // a round's pivots' buffer rows
+  int32_t* pslot = srow + kSlab;                                   // a round's pivots' buffer rows
   int32_t* ispiv = pslot + kSlab;  // 0: not a pivot column; else 1 + its pivot index
-  int32_t* prow = ispiv + ldS;
-  int32_t* pcol = prow + kBatchMax;
-  int* red = pcol + kBatchMax;
+  int16_t* prow = reinterpret_cast<int16_t*>(ispiv + ldN);  // pivot -> row (< kBatchMax)
+  int16_t* pcol = prow + kBatchMax;                          // pivot -> column
+  int* red = reinterpret_cast<int*>(pcol + kBatchMax);
   int* s_idx = red + kBatchWarps;
   // the final layout's index arrays reuse the multiplier space
-  int32_t* isprow = reinterpret_cast<int32_t*>(Ls);  // kSlab * kSlab = kBatchMax words
-  int32_t* rowpos = reinterpret_cast<int32_t*>(LT);  // kSlab * kRowBlock >= 2 kBatchMax words
+  int32_t* isprow = reinterpret_cast<int32_t*>(S);   // kSlab * ldS >= kBatchMax words
+  int32_t* rowpos = reinterpret_cast<int32_t*>(LT);  // kSlab * kLdL >= 2 kBatchMax words
   int32_t* colpos = rowpos + kBatchMax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* SC = scratch + (size_t)blockIdx.x * scratch_per_cta;
@@ -251,7 +423,7 @@ __global__ void __launch_bounds__(kBatchThreads)
       }
       continue;
     }
-    for (int j = tid; j < ldS; j += kBatchThreads) ispiv[j] = 0;
+    for (int j = tid; j < ldN; j += kBatchThreads) ispiv[j] = 0;
     __syncthreads();
     int r = 0, next = 0;
     while (next < m) {
@@ -261,11 +433,11 @@ __global__ void __launch_bounds__(kBatchThreads)
         // 1. rows next.. into buffer rows P..P+c-1, earlier slabs' pivot columns zeroed
         for (int i = warp; i < c; i += kBatchWarps) {
           const int s = P + i;
-          bt_load_row(S + (size_t)s * ldS, A + (int64_t)(next + i) * lda, n, ldS, [&](int j) {
+          bt_load_row(S + (size_t)s * ldS, A + (int64_t)(next + i) * lda, n, ldN, [&](int j) {
             const int f = ispiv[j];
             return f != 0 && f <= r;
           });
-          Ls[s * kSlab + lane] = 0u;
+          if (lane < kSlab) Ls[s * kSlab + lane] = 0u;
           if (lane == 0) srow[s] = next + i;
         }
         __syncthreads();
@@ -276,28 +448,27 @@ __global__ void __launch_bounds__(kBatchThreads)
             const uint32_t* st = S + (size_t)(P + tid) * ldS;
             for (int k = 0; k < P; ++k) {
               const int jk = spc[k];
-              Dot<kMode> s;
-              for (int q = 0; q < k; ++q) s.add(LT[q * kRowBlock + tid], S[(size_t)q * ldS + jk], F);
-              const uint32_t l = BF::mulm(invm[k], f_sub(st[jk], s.value(F), F), F);
+              const uint32_t sk = dot_prefix<kMode>(LT + tid, kLdL, S + jk, ldS, k, F);
+              const uint32_t l = BF::mulm(invm[k], f_sub(st[jk], sk, F), F);
               Ls[(P + tid) * kSlab + k] = l;
-              LT[k * kRowBlock + tid] = BF::to_mont(l, F);
+              LT[k * kLdL + tid] = BF::to_mont(l, F);
             }
           } else if (tid < kSlab) {
-            for (int k = 0; k < P; ++k) LT[k * kRowBlock + tid] = 0u;
+            for (int k = 0; k < P; ++k) LT[k * kLdL + tid] = 0u;
           }
           __syncthreads();
-          // ... then rows -= L U over every column: warp w takes rows 4w..4w+3,
-          // lane l columns c0 + l + 32 jj
-          const int rt = warp * 4;
-          for (int c0 = 0; c0 < n; c0 += 128) {
+          // ... then rows -= L U over every column: thread t takes rows
+          // 4 (t / kCL) .. + 3 and columns c0 + t % kCL + kCL jj
+          const int rt = (tid / kCL) * 4, cl = tid % kCL;
+          for (int c0 = 0; c0 < n; c0 += 4 * kCL) {
             Dot<kMode> acc[4][4];
 #pragma unroll 2
             for (int k = 0; k < P; ++k) {
-              const uint4 a4 = *reinterpret_cast<const uint4*>(LT + k * kRowBlock + rt);
+              const uint4 a4 = *reinterpret_cast<const uint4*>(LT + k * kLdL + rt);
               const uint32_t a[4] = {a4.x, a4.y, a4.z, a4.w};
               uint32_t bv[4];
 #pragma unroll
-              for (int jj = 0; jj < 4; ++jj) bv[jj] = S[(size_t)k * ldS + c0 + lane + 32 * jj];
+              for (int jj = 0; jj < 4; ++jj) bv[jj] = S[(size_t)k * ldS + c0 + cl + kCL * jj];
 #pragma unroll
               for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -307,7 +478,7 @@ __global__ void __launch_bounds__(kBatchThreads)
             for (int i = 0; i < 4; ++i)
 #pragma unroll
               for (int jj = 0; jj < 4; ++jj) {
-                const int row = rt + i, col = c0 + lane + 32 * jj;
+                const int row = rt + i, col = c0 + cl + kCL * jj;
                 if (row < c && col < n) {
                   uint32_t* e = S + (size_t)(P + row) * ldS + col;
                   *e = f_sub(*e, acc[i][jj].value(F), F);
@@ -330,64 +501,53 @@ __global__ void __launch_bounds__(kBatchThreads)
           if (lane == 0) first[P + i] = fz;
         }
         __syncthreads();
-        // 3. the new rows among themselves, in row order
+        // 3. the new rows among themselves, in row order: for each pivot, every
+        // warp looks up the inverse and updates its own rows below the pivot row
+        // (kRowUnroll chunks of 32 columns at a time), tracking their first
+        // non-zero; one barrier a pivot
         int np = 0;
-        const int nch = (n + 31) >> 5;
         for (int s = P; s < P + c; ++s) {
           const int js = first[s];
           if (js == INT_MAX) continue;  // a zero row: no pivot
           const int k = P + np;
           const uint32_t* pr = S + (size_t)s * ldS;
-          const int ub = s + 1, ue = P + c;
-          if (warp == 0) {
-            const uint32_t im = BF::to_mont(f_inv(pr[js], F, inv_table), F);
-            const int u = ub + lane;
-            if (u < ue) {
-              const uint32_t w = S[(size_t)u * ldS + js];
-              const uint32_t l = w != 0u ? BF::mulm(im, w, F) : 0u;
-              lrow[u] = l;
-              lmrow[u] = BF::to_mont(l, F);
-              Ls[u * kSlab + k] = l;
-              if (w != 0u) first[u] = INT_MAX;
+          const uint32_t im = BF::to_mont(f_inv(pr[js], F, inv_table), F);
+          for (int u = s + 1 + warp; u < P + c; u += kBatchWarps) {
+            uint32_t* ur = S + (size_t)u * ldS;
+            const uint32_t w = ur[js];
+            if (w == 0u) continue;  // unchanged; its first non-zero is not js
+            const uint32_t l = BF::mulm(im, w, F);
+            const uint32_t lm = BF::to_mont(l, F);
+            int fz = INT_MAX;  // this lane's first non-zero column, then the row's
+            for (int jb0 = 0; jb0 < n; jb0 += 32 * kRowUnroll) {
+              uint32_t nv[kRowUnroll];
+#pragma unroll
+              for (int q = 0; q < kRowUnroll; ++q) {
+                const int j = jb0 + 32 * q + lane;
+                nv[q] = j < n ? f_sub(ur[j], BF::mulm(lm, pr[j], F), F) : 0u;
+              }
+#pragma unroll
+              for (int q = 0; q < kRowUnroll; ++q) {
+                const int j = jb0 + 32 * q + lane;
+                if (j < n) ur[j] = nv[q];
+                if (nv[q] != 0u && fz == INT_MAX) fz = j;
+              }
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) fz = min(fz, __shfl_xor_sync(0xffffffffu, fz, o));
             if (lane == 0) {
-              spr[k] = srow[s];
-              spc[k] = js;
-              invm[k] = im;
-              pslot[np] = s;
-              ispiv[js] = r + k + 1;
+              Ls[u * kSlab + k] = l;
+              first[u] = fz;
             }
+          }
+          if (tid == 0) {
+            spr[k] = srow[s];
+            spc[k] = js;
+            invm[k] = im;
+            pslot[np] = s;
+            ispiv[js] = r + k + 1;
           }
           ++np;
-          __syncthreads();
-          // rank-1 update of the rows below it, as (row, 32-column chunk) items
-          const int items = (ue - ub) * nch;
-          for (int it0 = warp * kItemUnroll; it0 < items; it0 += kBatchWarps * kItemUnroll) {
-            uint32_t nv[kItemUnroll];
-            int iu[kItemUnroll], jb[kItemUnroll];
-            bool act[kItemUnroll];
-#pragma unroll
-            for (int q = 0; q < kItemUnroll; ++q) {
-              const int it = it0 + q;
-              const int du = it / nch;
-              iu[q] = ub + du;
-              jb[q] = (it - du * nch) * 32;
-              const uint32_t lm = it < items ? lmrow[iu[q]] : 0u;
-              act[q] = lm != 0u;
-              const int j = jb[q] + lane;
-              nv[q] = (act[q] && j < n)
-                          ? f_sub(S[(size_t)iu[q] * ldS + j], BF::mulm(lm, pr[j], F), F)
-                          : 0u;
-            }
-#pragma unroll
-            for (int q = 0; q < kItemUnroll; ++q) {
-              if (!act[q]) continue;  // warp-uniform
-              const int j = jb[q] + lane;
-              if (j < n) S[(size_t)iu[q] * ldS + j] = nv[q];
-              const unsigned nz = __ballot_sync(0xffffffffu, nv[q] != 0u);
-              if (nz && lane == 0) atomicMin(first + iu[q], jb[q] + __ffs(nz) - 1);
-            }
-          }
           __syncthreads();
         }
         // 4. rows without a pivot are final: back to the matrix (the multipliers
@@ -405,7 +565,7 @@ __global__ void __launch_bounds__(kBatchThreads)
         __syncthreads();
         // the round's pivot rows move up to buffer rows P..P+np-1 (pslot[i] >=
         // P + i, increasing: each column moved in increasing i)
-        for (int j = tid; j < ldS; j += kBatchThreads)
+        for (int j = tid; j < ldN; j += kBatchThreads)
           for (int i = 0; i < np; ++i)
             if (pslot[i] != P + i) S[(size_t)(P + i) * ldS + j] = S[(size_t)pslot[i] * ldS + j];
         if (tid < kSlab)
@@ -429,17 +589,39 @@ __global__ void __launch_bounds__(kBatchThreads)
         }
       }
       for (int k = tid; k < P; k += kBatchThreads) {
-        prow[r + k] = spr[k];
-        pcol[r + k] = spc[k];
+        prow[r + k] = (int16_t)spr[k];
+        pcol[r + k] = (int16_t)spc[k];
       }
       __syncthreads();
       // the rows below reduced by the slab's P pivots
       if (P > 0 && next < m) {
-        for (int rb = next; rb < m; rb += kRowBlock) {
-          const int nr = min(kRowBlock, m - rb);
-          if (tid < kRowBlock) {
+        if constexpr (kMode == 3) {
+          // U_JJ (plain), then W = U_JJ^{-1} U in place and U_JJ^{-1}, both in
+          // Montgomery form, by back substitution down each column:
+          // w_k = (u_k - sum_{q>k} U_k[j_q] w_q) / U_k[j_k]
+          uint32_t* Ujj = LT;  // [k][q], stride kSlab + 1; then X of a row block
+          for (int e = tid; e < P * P; e += kBatchThreads) {
+            const int k = e / P, q = e - k * P;
+            Ujj[k * (kSlab + 1) + q] = S[(size_t)k * ldS + spc[q]];
+          }
+          __syncthreads();
+          for (int col = tid; col < n + P; col += kBatchThreads) {
+            const bool ext = col >= n;
+            const int e = col - n;
+            uint32_t* w = ext ? Uinv + e : S + col;
+            const size_t ldw = ext ? (size_t)kLdE : (size_t)ldS;
+            for (int k = P - 1; k >= 0; --k) {
+              const uint32_t u = ext ? (k == e ? 1u : 0u) : w[(size_t)k * ldw];
+              Dot<kMode> d;
+              for (int q = k + 1; q < P; ++q) d.add(Ujj[k * (kSlab + 1) + q], w[(size_t)q * ldw], F);
+              w[(size_t)k * ldw] = BF::to_mont(BF::mulm(invm[k], f_sub(u, d.value(F), F), F), F);
+            }
+          }
+          __syncthreads();
+          uint32_t* XT = LT;  // [k][row], stride kLdL
+          for (int rb = next; rb < m; rb += kRowBlock) {
+            const int nr = min(kRowBlock, m - rb);
             if (tid < nr) {
-              // the row's entries at the pivot columns, then L by forward substitution
               const uint32_t* ar = A + (int64_t)(rb + tid) * lda;
               for (int k0 = 0; k0 < P; k0 += kLoadBatch) {
                 uint32_t x[kLoadBatch];
@@ -447,62 +629,86 @@ __global__ void __launch_bounds__(kBatchThreads)
                 for (int q = 0; q < kLoadBatch; ++q) x[q] = k0 + q < P ? ar[spc[k0 + q]] : 0u;
 #pragma unroll
                 for (int q = 0; q < kLoadBatch; ++q)
-                  if (k0 + q < P) LT[(k0 + q) * kRowBlock + tid] = x[q];
+                  if (k0 + q < P) XT[(k0 + q) * kLdL + tid] = x[q];
               }
-              for (int k = 0; k < P; ++k) {
-                const int jk = spc[k];
-                Dot<kMode> s;
-                for (int q = 0; q < k; ++q) s.add(LT[q * kRowBlock + tid], S[(size_t)q * ldS + jk], F);
-                const uint32_t l =
-                    BF::mulm(invm[k], f_sub(LT[k * kRowBlock + tid], s.value(F), F), F);
-                LT[k * kRowBlock + tid] = BF::to_mont(l, F);
-              }
-            } else {
-              for (int k = 0; k < P; ++k) LT[k * kRowBlock + tid] = 0u;
+            } else if (tid < kRowBlock) {
+              for (int k = 0; k < P; ++k) XT[k * kLdL + tid] = 0u;
             }
+            __syncthreads();
+            trailing_mma<kMode>(A + (int64_t)rb * lda, lda, nr, n, P, spc, XT, S, ldS, Uinv,
+                                ispiv, r, F);
+            __syncthreads();
           }
-          __syncthreads();
-          // C <- C - L U; the slab's pivot columns take L
-          const int tx = tid & 15, ty = tid >> 4;
-          for (int sub = 0; sub < nr; sub += kTile) {
-            const int rl = sub + ty * 4;  // first of this thread's rows within the block
-            for (int c0 = 0; c0 < n; c0 += kTile) {
-              uint32_t cv[4][4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                  const int row = rl + i, col = c0 + tx + 16 * jj;
-                  cv[i][jj] = (row < nr && col < n) ? A[(int64_t)(rb + row) * lda + col] : 0u;
+        } else {
+          for (int rb = next; rb < m; rb += kRowBlock) {
+            const int nr = min(kRowBlock, m - rb);
+            if (tid < kRowBlock) {
+              if (tid < nr) {
+                // the row's entries at the pivot columns, then L by forward substitution
+                const uint32_t* ar = A + (int64_t)(rb + tid) * lda;
+                for (int k0 = 0; k0 < P; k0 += kLoadBatch) {
+                  uint32_t x[kLoadBatch];
+  #pragma unroll
+                  for (int q = 0; q < kLoadBatch; ++q) x[q] = k0 + q < P ? ar[spc[k0 + q]] : 0u;
+  #pragma unroll
+                  for (int q = 0; q < kLoadBatch; ++q)
+                    if (k0 + q < P) LT[(k0 + q) * kLdL + tid] = x[q];
                 }
-              Dot<kMode> acc[4][4];
-#pragma unroll 2
-              for (int k = 0; k < P; ++k) {
-                const uint4 a4 = *reinterpret_cast<const uint4*>(LT + k * kRowBlock + rl);
-                const uint32_t a[4] = {a4.x, a4.y, a4.z, a4.w};
-                uint32_t bv[4];
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) bv[jj] = S[(size_t)k * ldS + c0 + tx + 16 * jj];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                  for (int jj = 0; jj < 4; ++jj) acc[i][jj].add(a[i], bv[jj], F);
+                for (int k = 0; k < P; ++k) {
+                  const int jk = spc[k];
+                  const uint32_t sk = dot_prefix<kMode>(LT + tid, kLdL, S + jk, ldS, k, F);
+                  const uint32_t l = BF::mulm(invm[k], f_sub(LT[k * kLdL + tid], sk, F), F);
+                  LT[k * kLdL + tid] = BF::to_mont(l, F);
+                }
+              } else {
+                for (int k = 0; k < P; ++k) LT[k * kLdL + tid] = 0u;
               }
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                  const int row = rl + i, col = c0 + tx + 16 * jj;
-                  if (row < nr && col < n) {
-                    const int f = ispiv[col];
-                    const uint32_t v = f > r ? BF::from_mont(LT[(f - r - 1) * kRowBlock + row], F)
-                                             : f_sub(cv[i][jj], acc[i][jj].value(F), F);
-                    A[(int64_t)(rb + row) * lda + col] = v;
+            }
+            __syncthreads();
+            // C <- C - L U; the slab's pivot columns take L
+            {
+              const int tx = tid & 15, ty = tid >> 4;
+              for (int sub = 0; sub < nr; sub += kTile) {
+                const int rl = sub + ty * 4;  // first of this thread's rows within the block
+                for (int c0 = 0; c0 < n; c0 += kTile) {
+                  uint32_t cv[4][4];
+    #pragma unroll
+                  for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                      const int row = rl + i, col = c0 + tx + 16 * jj;
+                      cv[i][jj] = (row < nr && col < n) ? A[(int64_t)(rb + row) * lda + col] : 0u;
+                    }
+                  Dot<kMode> acc[4][4];
+    #pragma unroll 2
+                  for (int k = 0; k < P; ++k) {
+                    const uint4 a4 = *reinterpret_cast<const uint4*>(LT + k * kLdL + rl);
+                    const uint32_t a[4] = {a4.x, a4.y, a4.z, a4.w};
+                    uint32_t bv[4];
+    #pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) bv[jj] = S[(size_t)k * ldS + c0 + tx + 16 * jj];
+    #pragma unroll
+                    for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                      for (int jj = 0; jj < 4; ++jj) acc[i][jj].add(a[i], bv[jj], F);
                   }
+    #pragma unroll
+                  for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                      const int row = rl + i, col = c0 + tx + 16 * jj;
+                      if (row < nr && col < n) {
+                        const int f = ispiv[col];
+                        const uint32_t v = f > r ? BF::from_mont(LT[(f - r - 1) * kLdL + row], F)
+                                                 : f_sub(cv[i][jj], acc[i][jj].value(F), F);
+                        A[(int64_t)(rb + row) * lda + col] = v;
+                      }
+                    }
                 }
+              }
             }
+            __syncthreads();
           }
-          __syncthreads();
         }
       }
       r += P;
@@ -532,7 +738,7 @@ __global__ void __launch_bounds__(kBatchThreads)
     for (int t0 = 0; t0 < r; t0 += kBatchWarps) {
       const int t = t0 + warp;
       uint32_t* w = S + (size_t)warp * ldS;
-      if (t < r) bt_load_row(w, A + (int64_t)rowpos[t] * lda, n, ldS, [](int) { return false; });
+      if (t < r) bt_load_row(w, A + (int64_t)rowpos[t] * lda, n, ldN, [](int) { return false; });
       __syncthreads();
       if (t < r) {
         uint32_t* dst = A + (int64_t)t * lda;
@@ -560,21 +766,67 @@ __global__ void k_batch_reset(int* counter) { *counter = 0; }
 
 int slab_ld(int max_n) { return (int)cdiv(std::max(max_n, 1), kLd) * kLd; }
 
-size_t slab_smem_bytes(int max_n) { return sizeof(uint32_t) * slab_smem_words(slab_ld(max_n)); }
+template <int kSlab>
+size_t slab_smem_bytes(int max_n) { return sizeof(uint32_t) * slab_smem_words<kSlab>(slab_ld(max_n)); }
 
-template <int kMode>
-int batched_occupancy(size_t smem) {
-  if (cudaFuncSetAttribute(k_batched_pluq<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           227 * 1024) != cudaSuccess)
+template <int kMode, int kSlab>
+int batched_occupancy(int max_n) {
+  if (cudaFuncSetAttribute(k_batched_pluq<kMode, kSlab>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
     return 0;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_pluq<kMode>, kBatchThreads,
-                                                    smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_pluq<kMode, kSlab>,
+                                                    kBatchThreads,
+                                                    slab_smem_bytes<kSlab>(max_n)) != cudaSuccess)
     return 0;
   return occ;
 }
 
-int batched_mode(const FieldP& F) { return F.is2 ? 0 : (F.p < (1u << 27) ? 1 : 2); }
+int batched_mode(const FieldP& F) {
+  return F.is2 ? 0 : F.p < (1u << 16) ? 3 : F.p < (1u << 27) ? 1 : 2;
+}
+
+// Buffer height: the option's, else 16 (measured fastest on the batch of 4096
+// matrices of 32..512 rows and columns over GF(65521): 10.6 ms against 11.3 for
+// 24 and 12.1 for 32).
+int batched_slab(const pluq_ctx* c, int max_n) {
+  (void)max_n;
+  return c->batch_slab ? c->batch_slab : 16;
+}
+
+template <int kMode>
+int occupancy_for(int slab, int max_n) {
+  switch (slab) {
+    case 16: return batched_occupancy<kMode, 16>(max_n);
+    case 24: return batched_occupancy<kMode, 24>(max_n);
+    default: return batched_occupancy<kMode, 32>(max_n);
+  }
+}
+
+template <int kMode, int kSlab>
+void launch_slab(pluq_ctx* c, int G, const BatchDesc* d, const int32_t* order, int count,
+                 int* counter, uint32_t* sc, size_t per, int max_n, int64_t* ranks,
+                 int32_t* status) {
+  k_batched_pluq<kMode, kSlab><<<G, kBatchThreads, slab_smem_bytes<kSlab>(max_n), c->stream>>>(
+      d, order, count, counter, c->F, inv_table_ptr(c), sc, per, slab_ld(max_n), ranks, status);
+}
+
+template <int kMode>
+void launch_mode(pluq_ctx* c, int slab, int G, const BatchDesc* d, const int32_t* order,
+                 int count, int* counter, uint32_t* sc, size_t per, int max_n, int64_t* ranks,
+                 int32_t* status) {
+  switch (slab) {
+    case 16:
+      launch_slab<kMode, 16>(c, G, d, order, count, counter, sc, per, max_n, ranks, status);
+      break;
+    case 24:
+      launch_slab<kMode, 24>(c, G, d, order, count, counter, sc, per, max_n, ranks, status);
+      break;
+    default:
+      launch_slab<kMode, 32>(c, G, d, order, count, counter, sc, per, max_n, ranks, status);
+      break;
+  }
+}
 
 }  // namespace
 
@@ -582,12 +834,13 @@ int batched_max_dim() { return kBatchMax; }
 
 // CTAs of the persistent launch for matrices of at most max_n columns.
 int batched_grid(pluq_ctx* c, int max_n) {
-  const size_t smem = slab_smem_bytes(max_n);
+  const int slab = batched_slab(c, max_n);
   int occ = 0;
   switch (batched_mode(c->F)) {
-    case 0: occ = batched_occupancy<0>(smem); break;
-    case 1: occ = batched_occupancy<1>(smem); break;
-    default: occ = batched_occupancy<2>(smem); break;
+    case 0: occ = occupancy_for<0>(slab, max_n); break;
+    case 1: occ = occupancy_for<1>(slab, max_n); break;
+    case 2: occ = occupancy_for<2>(slab, max_n); break;
+    default: occ = occupancy_for<3>(slab, max_n); break;
   }
   return occ > 0 ? occ * c->sm_count : 0;
 }
@@ -606,22 +859,20 @@ int launch_batched(pluq_ctx* c, const void* descs, const int32_t* order, int cou
   }
   ProfScope ps(c, PC_BASE);
   const auto* d = static_cast<const BatchDesc*>(descs);
-  const int ldS = slab_ld(max_n);
-  const size_t smem = slab_smem_bytes(max_n);
+  const int slab = batched_slab(c, max_n);
   uint32_t* sc = c->batch_scratch.as<uint32_t>();
-  const uint32_t* tab = inv_table_ptr(c);
   switch (batched_mode(c->F)) {
     case 0:
-      k_batched_pluq<0><<<G, kBatchThreads, smem, c->stream>>>(d, order, count, counter, c->F, tab,
-                                                               sc, per, ldS, ranks, status);
+      launch_mode<0>(c, slab, G, d, order, count, counter, sc, per, max_n, ranks, status);
       break;
     case 1:
-      k_batched_pluq<1><<<G, kBatchThreads, smem, c->stream>>>(d, order, count, counter, c->F, tab,
-                                                               sc, per, ldS, ranks, status);
+      launch_mode<1>(c, slab, G, d, order, count, counter, sc, per, max_n, ranks, status);
+      break;
+    case 2:
+      launch_mode<2>(c, slab, G, d, order, count, counter, sc, per, max_n, ranks, status);
       break;
     default:
-      k_batched_pluq<2><<<G, kBatchThreads, smem, c->stream>>>(d, order, count, counter, c->F, tab,
-                                                               sc, per, ldS, ranks, status);
+      launch_mode<3>(c, slab, G, d, order, count, counter, sc, per, max_n, ranks, status);
       break;
   }
   PLUQ_CUDA(cudaGetLastError());

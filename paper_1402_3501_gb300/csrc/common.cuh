@@ -180,6 +180,8 @@ struct pluq_ctx {
   int batch_graph_count = -1;
   int64_t batch_graph_elems = 0;
   int batch_graph_maxn = 0;          // widest matrix the captured launch was sized for
+  int batch_graph_slab = 0;          // buffer height the captured launch was made for
+  int batch_slab = 0;                // batched buffer height (PLUQ_OPT_BATCH_SLAB), 0: by width
   uint32_t batch_graph_p = 0;        // field and inverse table baked into the graph
   const void* batch_graph_tab = nullptr;
   DevBuf batch_scratch;    // per-CTA gather scratch of the batched kernel

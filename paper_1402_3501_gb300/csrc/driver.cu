@@ -1192,7 +1192,7 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
     // D2H ranks and status
     if (c->batch_graph && (c->batch_graph_count != cnt || c->batch_graph_key != db ||
                            old_dev != c->batch_dev.ptr || c->batch_graph_elems < max_elems ||
-                           c->batch_graph_maxn != max_n ||
+                           c->batch_graph_maxn != max_n || c->batch_graph_slab != c->batch_slab ||
                            c->batch_graph_p != c->F.p ||
                            c->batch_graph_tab != (const void*)inv_table_ptr(c))) {
       cudaGraphExecDestroy(c->batch_graph);
@@ -1238,6 +1238,7 @@ int pluq_modp_batched(pluq_ctx* c, uint32_t p, int32_t batch, const int64_t* m, 
       c->batch_graph_key = db;
       c->batch_graph_elems = max_elems;
       c->batch_graph_maxn = max_n;
+      c->batch_graph_slab = c->batch_slab;
       c->batch_graph_p = c->F.p;
       c->batch_graph_tab = inv_table_ptr(c);
     }
@@ -1401,6 +1402,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_WINOGRAD_MIN:
       if (value < 0) return PLUQ_ERR_INVALID_ARG;
       c->wino_min = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_BATCH_SLAB:
+      if (value != 0 && value != 16 && value != 24 && value != 32) return PLUQ_ERR_INVALID_ARG;
+      c->batch_slab = value;
       return PLUQ_OK;
     case PLUQ_OPT_WORKSPACE_MB:
       if (value < 0) return PLUQ_ERR_INVALID_ARG;

@@ -747,11 +747,12 @@ def _batch_cases(p, seed):
     return cases
 
 
-@pytest.mark.parametrize("p", [2, 65521, 131071, 134217757, 2147483647])
+@pytest.mark.parametrize("p", [2, 3, 65521, 131071, 134217757, 2147483647])
 def test_batched_parity(ctx, p):
     """Every matrix of a mixed batch (empty, one-row, one-column, rank-deficient,
     the widest the persistent kernel takes, one past it) against the oracle, for
-    each of the slab kernel's field modes: p = 2, p < 2^27 (one reduction per dot
+    each of the slab kernel's field modes: p = 2, p < 2^16 (the update below a
+    slab on the tensor cores, 8-bit digits), p < 2^27 (one reduction per dot
     product) and larger p (a reduction per product)."""
     cases = _batch_cases(p, 3)
     As = [to_dev(A) for A in cases]
@@ -765,6 +766,28 @@ def test_batched_parity(ctx, p):
             P, Q = P.cpu().numpy(), Q.cpu().numpy()
             check_rpm_from_pq(P, Q, r, ref.rpm)
             check_pluq(A, p, P, Q, Ad.cpu().numpy().astype(np.int64), r)
+
+
+@pytest.mark.parametrize("slab", [16, 24, 32])
+def test_batched_slab_heights(slab):
+    """Each buffer height of the batched kernel (pivots a slab collects before
+    updating the rows below) against the oracle on the mixed batch."""
+    p = 65521
+    c = pq.Context(0)
+    try:
+        c.set_option("batch_slab", slab)
+        cases = _batch_cases(p, 5)
+        As = [to_dev(A) for A in cases]
+        ranks, Ps, Qs = pq.pluq_modp_batched(As, p, ctx=c)
+        torch.cuda.synchronize()
+        for A, Ad, r, P, Q in zip(cases, As, ranks, Ps, Qs):
+            ref = oracle.pluq(A, p)
+            assert r == ref.rank
+            P, Q = P.cpu().numpy(), Q.cpu().numpy()
+            check_rpm_from_pq(P, Q, r, ref.rpm)
+            check_pluq(A, p, P, Q, Ad.cpu().numpy().astype(np.int64), r)
+    finally:
+        c.close()
 
 
 @pytest.mark.parametrize("p", [2, 65521])
