@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <climits>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -120,8 +121,8 @@ struct Dot {
 // sum_{q < k} a[q lda] b[q ldb] (a Montgomery, b plain) as a plain residue, in
 // four independent partial sums (k <= 32: the merged sum stays below p 2^32
 // in mode 1)
-template <int kMode>
-__device__ __forceinline__ uint32_t dot_prefix(const uint32_t* a, int lda, const uint32_t* b,
+template <int kMode, typename TB>
+__device__ __forceinline__ uint32_t dot_prefix(const uint32_t* a, int lda, const TB* b,
                                                size_t ldb, int k, const FieldP& F) {
   Dot<kMode> s0, s1, s2, s3;
   int q = 0;
@@ -180,9 +181,8 @@ __device__ void bt_compact(const int32_t* flag, int cnt, int32_t* out, int base,
 
 // n words of row src (global) into dst (shared), zero where drop(j), zero
 // from n to ld; kLoadBatch loads of a lane in flight.  One warp.
-template <typename Drop>
-__device__ __forceinline__ void bt_load_row(uint32_t* dst, const uint32_t* src, int n, int ld,
-                                            Drop drop) {
+template <typename T, typename Drop>
+__device__ __forceinline__ void bt_load_row(T* dst, const uint32_t* src, int n, int ld, Drop drop) {
   const int lane = threadIdx.x & 31;
   for (int jb0 = 0; jb0 < ld; jb0 += 32 * kLoadBatch) {
     uint32_t v[kLoadBatch];
@@ -194,7 +194,7 @@ __device__ __forceinline__ void bt_load_row(uint32_t* dst, const uint32_t* src, 
 #pragma unroll
     for (int q = 0; q < kLoadBatch; ++q) {
       const int j = jb0 + 32 * q + lane;
-      if (j < ld) dst[j] = v[q];
+      if (j < ld) dst[j] = (T)v[q];
     }
   }
 }
@@ -229,20 +229,26 @@ __device__ __forceinline__ uint32_t f2u_exact(float x) {
   return __float_as_uint(x + 8388608.0f) & 0x7FFFFFu;
 }
 
-// CTAs an SM the register budget is set for, by buffer height.
-__host__ __device__ constexpr int slab_min_blocks(int slab) { return slab >= 32 ? 2 : 3; }
+// Buffer storage: 16-bit residues for p < 2^16 (mode 3), else 32-bit.
+template <int kMode>
+using SlabT = std::conditional_t<kMode == 3, uint16_t, uint32_t>;
 
-// Shared memory of one CTA, in 32-bit words, for buffer rows of ldN columns.
-template <int kSlab>
-__host__ __device__ constexpr size_t slab_smem_words(int ldN) {
-  return (size_t)kSlab * (ldN + kPadS)    // S: pivot rows, then candidate rows
-         + (size_t)kSlab * kLdL           // LT: multipliers (or entries) of a row block, pivot-major
-         + (size_t)kSlab * kLdE           // Uinv: U_JJ^{-1} of the tensor-core update
-         + (size_t)kSlab * kSlab          // Ls: multipliers of the buffer rows (plain)
-         + 6 * kSlab                      // spr, spc, invm, first, srow, pslot
-         + (size_t)ldN                    // ispiv
-         + (size_t)kBatchMax              // prow, pcol (16-bit)
-         + kBatchWarps + 8;               // red, misc
+// CTAs an SM the register budget is set for.
+__host__ __device__ constexpr int slab_min_blocks(int slab, bool narrow) {
+  return (slab >= 32 && !narrow) ? 2 : 3;
+}
+
+// Shared memory of one CTA, in bytes, for buffer rows of ldN columns of TS.
+template <int kSlab, typename TS>
+__host__ __device__ constexpr size_t slab_smem_bytes_for(int ldN) {
+  return sizeof(TS) * ((size_t)kSlab * (ldN + kPadS)  // S: pivot rows, then candidate rows
+                       + (size_t)kSlab * kLdE)        // Uinv: U_JJ^{-1} of the tensor-core update
+         + 4 * ((size_t)kSlab * kLdL                  // LT: multipliers (or entries) of a row block
+                + (size_t)kSlab * kSlab               // Ls: multipliers of the buffer rows (plain)
+                + 6 * kSlab                      // spr, spc, invm, first, srow, pslot
+                + (size_t)ldN                    // ispiv
+                + (size_t)kBatchMax              // prow, pcol (16-bit)
+                + kBatchWarps + 8);              // red, misc
 }
 
 
@@ -261,11 +267,11 @@ __host__ __device__ constexpr size_t slab_smem_words(int ldN) {
 // Warp w takes rows 16w..16w+15 of the block (its A fragments stay in
 // registers) and sweeps the columns 16 at a time, then the P columns of
 // U_JJ^{-1}.
-template <int kMode>
+template <int kMode, typename TS>
 __device__ __forceinline__ void trailing_mma(uint32_t* C, int64_t ldc, int nr, int n, int P,
-                                             const int32_t* spc, const uint32_t* XT,
-                                             const uint32_t* S, int ldS, const uint32_t* Uinv,
-                                             const int32_t* ispiv, int r, const FieldP& F) {
+                                             const int32_t* spc, const uint32_t* XT, const TS* S,
+                                             int ldS, const TS* Uinv, const int32_t* ispiv, int r,
+                                             const FieldP& F) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int m0 = warp * 16;
@@ -347,7 +353,7 @@ __device__ __forceinline__ void trailing_mma(uint32_t* C, int64_t ldc, int nr, i
 }
 
 template <int kMode, int kSlab>
-__global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
+__global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab, kMode == 3))
     k_batched_pluq(const BatchDesc* __restrict__ descs, const int32_t* __restrict__ order,
                    int batch, int* __restrict__ counter, FieldP F,
                    const uint32_t* __restrict__ inv_table, uint32_t* __restrict__ scratch,
@@ -357,12 +363,13 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
   constexpr int kMinFree = kSlab / 4;  // a slab closes when fewer buffer rows are free
   constexpr int kRG = kSlab <= 16 ? 4 : 8;   // row groups of 4 in the refill update
   constexpr int kCL = kBatchThreads / kRG;   // column lanes: the update's tile is 4 kCL wide
+  using TS = SlabT<kMode>;
   extern __shared__ __align__(16) uint32_t smem[];
   const int ldS = ldN + kPadS;  // row stride of the buffer
-  uint32_t* S = smem;
-  uint32_t* LT = S + (size_t)kSlab * ldS;
-  uint32_t* Uinv = LT + kSlab * kLdL;
-  uint32_t* Ls = Uinv + kSlab * kLdE;
+  TS* S = reinterpret_cast<TS*>(smem);
+  uint32_t* LT = reinterpret_cast<uint32_t*>(S + (size_t)kSlab * ldS);
+  TS* Uinv = reinterpret_cast<TS*>(LT + kSlab * kLdL);
+  uint32_t* Ls = reinterpret_cast<uint32_t*>(Uinv + kSlab * kLdE);
   int32_t* spr = reinterpret_cast<int32_t*>(Ls + kSlab * kSlab);  // slab pivot -> matrix row
   int32_t* spc = spr + kSlab;                                      // slab pivot -> column
   uint32_t* invm = reinterpret_cast<uint32_t*>(spc + kSlab);       // inverse pivot (Montgomery)
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
           // 2. their multipliers for the slab's pivots (forward substitution on the
           // pivot columns, a thread a row) ...
           if (tid < c) {
-            const uint32_t* st = S + (size_t)(P + tid) * ldS;
+            const TS* st = S + (size_t)(P + tid) * ldS;
             for (int k = 0; k < P; ++k) {
               const int jk = spc[k];
               const uint32_t sk = dot_prefix<kMode>(LT + tid, kLdL, S + jk, ldS, k, F);
@@ -480,8 +487,8 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
               for (int jj = 0; jj < 4; ++jj) {
                 const int row = rt + i, col = c0 + cl + kCL * jj;
                 if (row < c && col < n) {
-                  uint32_t* e = S + (size_t)(P + row) * ldS + col;
-                  *e = f_sub(*e, acc[i][jj].value(F), F);
+                  TS* e = S + (size_t)(P + row) * ldS + col;
+                  *e = (TS)f_sub(*e, acc[i][jj].value(F), F);
                 }
               }
           }
@@ -489,7 +496,7 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
         }
         // first non-zero of each new row
         for (int i = warp; i < c; i += kBatchWarps) {
-          const uint32_t* st = S + (size_t)(P + i) * ldS;
+          const TS* st = S + (size_t)(P + i) * ldS;
           int fz = INT_MAX;
           for (int jb = 0; jb < n; jb += 32) {
             const unsigned nz = __ballot_sync(0xffffffffu, jb + lane < n && st[jb + lane] != 0u);
@@ -510,10 +517,10 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
           const int js = first[s];
           if (js == INT_MAX) continue;  // a zero row: no pivot
           const int k = P + np;
-          const uint32_t* pr = S + (size_t)s * ldS;
+          const TS* pr = S + (size_t)s * ldS;
           const uint32_t im = BF::to_mont(f_inv(pr[js], F, inv_table), F);
           for (int u = s + 1 + warp; u < P + c; u += kBatchWarps) {
-            uint32_t* ur = S + (size_t)u * ldS;
+            TS* ur = S + (size_t)u * ldS;
             const uint32_t w = ur[js];
             if (w == 0u) continue;  // unchanged; its first non-zero is not js
             const uint32_t l = BF::mulm(im, w, F);
@@ -529,7 +536,7 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
 #pragma unroll
               for (int q = 0; q < kRowUnroll; ++q) {
                 const int j = jb0 + 32 * q + lane;
-                if (j < n) ur[j] = nv[q];
+                if (j < n) ur[j] = (TS)nv[q];
                 if (nv[q] != 0u && fz == INT_MAX) fz = j;
               }
             }
@@ -580,7 +587,7 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
       // the slab's earlier pivots, the reduced row elsewhere
       for (int k = warp; k < P; k += kBatchWarps) {
         uint32_t* row = A + (int64_t)spr[k] * lda;
-        const uint32_t* st = S + (size_t)k * ldS;
+        const TS* st = S + (size_t)k * ldS;
         for (int j = lane; j < n; j += 32) {
           const int f = ispiv[j];
           if (f != 0 && f <= r) continue;
@@ -608,13 +615,13 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
           for (int col = tid; col < n + P; col += kBatchThreads) {
             const bool ext = col >= n;
             const int e = col - n;
-            uint32_t* w = ext ? Uinv + e : S + col;
+            TS* w = ext ? Uinv + e : S + col;
             const size_t ldw = ext ? (size_t)kLdE : (size_t)ldS;
             for (int k = P - 1; k >= 0; --k) {
               const uint32_t u = ext ? (k == e ? 1u : 0u) : w[(size_t)k * ldw];
               Dot<kMode> d;
               for (int q = k + 1; q < P; ++q) d.add(Ujj[k * (kSlab + 1) + q], w[(size_t)q * ldw], F);
-              w[(size_t)k * ldw] = BF::to_mont(BF::mulm(invm[k], f_sub(u, d.value(F), F), F), F);
+              w[(size_t)k * ldw] = (TS)BF::to_mont(BF::mulm(invm[k], f_sub(u, d.value(F), F), F), F);
             }
           }
           __syncthreads();
@@ -737,7 +744,7 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab))
     // rowpos[t] >= t, and rows below t0 + 8 are not read again
     for (int t0 = 0; t0 < r; t0 += kBatchWarps) {
       const int t = t0 + warp;
-      uint32_t* w = S + (size_t)warp * ldS;
+      TS* w = S + (size_t)warp * ldS;
       if (t < r) bt_load_row(w, A + (int64_t)rowpos[t] * lda, n, ldN, [](int) { return false; });
       __syncthreads();
       if (t < r) {
@@ -766,8 +773,10 @@ __global__ void k_batch_reset(int* counter) { *counter = 0; }
 
 int slab_ld(int max_n) { return (int)cdiv(std::max(max_n, 1), kLd) * kLd; }
 
-template <int kSlab>
-size_t slab_smem_bytes(int max_n) { return sizeof(uint32_t) * slab_smem_words<kSlab>(slab_ld(max_n)); }
+template <int kMode, int kSlab>
+size_t slab_smem_bytes(int max_n) {
+  return slab_smem_bytes_for<kSlab, SlabT<kMode>>(slab_ld(max_n));
+}
 
 template <int kMode, int kSlab>
 int batched_occupancy(int max_n) {
@@ -777,7 +786,7 @@ int batched_occupancy(int max_n) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_pluq<kMode, kSlab>,
                                                     kBatchThreads,
-                                                    slab_smem_bytes<kSlab>(max_n)) != cudaSuccess)
+                                                    slab_smem_bytes<kMode, kSlab>(max_n)) != cudaSuccess)
     return 0;
   return occ;
 }
@@ -786,12 +795,12 @@ int batched_mode(const FieldP& F) {
   return F.is2 ? 0 : F.p < (1u << 16) ? 3 : F.p < (1u << 27) ? 1 : 2;
 }
 
-// Buffer height: the option's, else 16 (measured fastest on the batch of 4096
-// matrices of 32..512 rows and columns over GF(65521): 10.6 ms against 11.3 for
-// 24 and 12.1 for 32).
+// Buffer height: the option's, else 32 for p < 2^16 (16-bit buffer: three CTAs
+// an SM at 512 columns), 16 otherwise.
 int batched_slab(const pluq_ctx* c, int max_n) {
   (void)max_n;
-  return c->batch_slab ? c->batch_slab : 16;
+  if (c->batch_slab) return c->batch_slab;
+  return batched_mode(c->F) == 3 ? 32 : 16;
 }
 
 template <int kMode>
@@ -807,7 +816,8 @@ template <int kMode, int kSlab>
 void launch_slab(pluq_ctx* c, int G, const BatchDesc* d, const int32_t* order, int count,
                  int* counter, uint32_t* sc, size_t per, int max_n, int64_t* ranks,
                  int32_t* status) {
-  k_batched_pluq<kMode, kSlab><<<G, kBatchThreads, slab_smem_bytes<kSlab>(max_n), c->stream>>>(
+  k_batched_pluq<kMode, kSlab><<<G, kBatchThreads, slab_smem_bytes<kMode, kSlab>(max_n),
+                                 c->stream>>>(
       d, order, count, counter, c->F, inv_table_ptr(c), sc, per, slab_ld(max_n), ranks, status);
 }
 
