@@ -92,6 +92,14 @@ struct BField {
   }
 };
 
+// REDC(t) for t < 2^32: t + m p vanishes mod 2^32 (m = -t p^{-1} mod 2^32), so
+// (t + m p) / 2^32 is the high word of m p plus the carry out of the low
+// words, which is 1 exactly when t != 0; the result is at most p.
+__device__ __forceinline__ uint32_t f_redc32(uint32_t t, const FieldP& F) {
+  const uint32_t u = __umulhi(t * F.pneg_inv, F.p) + (t != 0u ? 1u : 0u);
+  return u >= F.p ? u - F.p : u;
+}
+
 // sum of Montgomery a times plain b over a dot product, as a plain residue
 template <int kMode>
 struct Dot {
@@ -526,18 +534,46 @@ __global__ void __launch_bounds__(kBatchThreads, slab_min_blocks(kSlab, kMode ==
             const uint32_t l = BF::mulm(im, w, F);
             const uint32_t lm = BF::to_mont(l, F);
             int fz = INT_MAX;  // this lane's first non-zero column, then the row's
-            for (int jb0 = 0; jb0 < n; jb0 += 32 * kRowUnroll) {
-              uint32_t nv[kRowUnroll];
+            if constexpr (kMode == 3) {
+              // 16-bit residues two at a time (32-bit shared accesses); the
+              // products are below 2^32, so a 32-bit Montgomery reduction
+              const uint32_t* pr2 = reinterpret_cast<const uint32_t*>(pr);
+              uint32_t* ur2 = reinterpret_cast<uint32_t*>(ur);
+              const int n2 = (n + 1) >> 1;  // an odd n pairs with the zero column n
+              for (int jb0 = 0; jb0 < n2; jb0 += 32 * kRowUnroll) {
+                uint32_t nv[kRowUnroll];
 #pragma unroll
-              for (int q = 0; q < kRowUnroll; ++q) {
-                const int j = jb0 + 32 * q + lane;
-                nv[q] = j < n ? f_sub(ur[j], BF::mulm(lm, pr[j], F), F) : 0u;
+                for (int q = 0; q < kRowUnroll; ++q) {
+                  const int j2 = jb0 + 32 * q + lane;
+                  nv[q] = 0u;
+                  if (j2 < n2) {
+                    const uint32_t a = ur2[j2], b = pr2[j2];
+                    const uint32_t lo = f_sub(a & 0xFFFFu, f_redc32(lm * (b & 0xFFFFu), F), F);
+                    const uint32_t hi = f_sub(a >> 16, f_redc32(lm * (b >> 16), F), F);
+                    nv[q] = lo | (hi << 16);
+                  }
+                }
+#pragma unroll
+                for (int q = 0; q < kRowUnroll; ++q) {
+                  const int j2 = jb0 + 32 * q + lane;
+                  if (j2 < n2) ur2[j2] = nv[q];
+                  if (nv[q] != 0u && fz == INT_MAX) fz = 2 * j2 + ((nv[q] & 0xFFFFu) ? 0 : 1);
+                }
               }
+            } else {
+              for (int jb0 = 0; jb0 < n; jb0 += 32 * kRowUnroll) {
+                uint32_t nv[kRowUnroll];
 #pragma unroll
-              for (int q = 0; q < kRowUnroll; ++q) {
-                const int j = jb0 + 32 * q + lane;
-                if (j < n) ur[j] = (TS)nv[q];
-                if (nv[q] != 0u && fz == INT_MAX) fz = j;
+                for (int q = 0; q < kRowUnroll; ++q) {
+                  const int j = jb0 + 32 * q + lane;
+                  nv[q] = j < n ? f_sub(ur[j], BF::mulm(lm, pr[j], F), F) : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < kRowUnroll; ++q) {
+                  const int j = jb0 + 32 * q + lane;
+                  if (j < n) ur[j] = (TS)nv[q];
+                  if (nv[q] != 0u && fz == INT_MAX) fz = j;
+                }
               }
             }
 #pragma unroll
