@@ -342,6 +342,11 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
  *                        slab's pivots (the most pivots one update of the rows
  *                        below carries); smaller buffers fit more CTAs an SM.
  *                        0: 16.
+ *   PLUQ_OPT_LOOKAHEAD   0 (default) or 1: where A1 has full rank (F and G
+ *                        empty) and R splits further, H's update is split at R's
+ *                        first quarter: H11 first, the rest on a third stream
+ *                        while R's recursion factors H11 (results are identical;
+ *                        the third stream's workspace is sized for H).
  * Errors: INVALID_ARG for an unknown option or a value out of range. */
 #define PLUQ_OPT_LEAF_DIM 1
 #define PLUQ_OPT_LEAF_KIND 2
@@ -362,6 +367,7 @@ int pluq_set_tuning(pluq_ctx* ctx, int bm, int bn, int trsm_block);
 #define PLUQ_OPT_FUSED_KMAX 17
 #define PLUQ_OPT_DIAG_INVERSES 18
 #define PLUQ_OPT_BATCH_SLAB 19
+#define PLUQ_OPT_LOOKAHEAD 20
 int pluq_set_option(pluq_ctx* ctx, int option, int value);
 
 /* Largest block (rows and columns, 0..2048) factored as one leaf by a

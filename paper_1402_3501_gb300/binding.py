@@ -148,7 +148,7 @@ class Context:
                "decomposition": 10, "slab_rows": 11, "wait_limit_us": 12, "workspace_mb": 13,
                "winograd_min": 14, "fgemm_tile": 15, "trsm_strip": 16,
                "fused_kmax": 17, "diag_inverses": 18,
-               "batch_slab": 19}
+               "batch_slab": 19, "lookahead": 20}
 
     def set_option(self, name: str, value: int):
         """Set a recursion option (see PLUQ_OPT_* in include/pluqmodp.h)."""

@@ -150,6 +150,8 @@ struct pluq_ctx {
   cudaStream_t own_stream = nullptr;  // a child context's stream
   cudaEvent_t fork_ev = nullptr;      // recorded before F and G start
   cudaEvent_t side_ev[2] = {nullptr, nullptr};  // E ready, G updated (two-stream update)
+  std::vector<cudaEvent_t> la_ev;    // look-ahead events, two a recursion depth
+  int lookahead = 0;                 // PLUQ_OPT_LOOKAHEAD
   FieldP F{};
   int form = PLUQ_FORM_FP64;
   int bm = 128, bn = 128;  // base-case tile
@@ -214,7 +216,7 @@ struct pluq_ctx {
   int slab_rows = 0;              // 0: the leaf cut-off
   int lane_depth = 0;             // 0 for the user's context
   pluq_ctx* parent = nullptr;
-  pluq_ctx* lane[2] = {nullptr, nullptr};
+  pluq_ctx* lane[3] = {nullptr, nullptr, nullptr};  // F, G (and side updates), look-ahead
   // schedules chosen by pluq_autotune, per (p, m, n, form); applied by every
   // factorization of a matching shape unless use_tuned is 0
   struct Tuned {

@@ -273,6 +273,9 @@ void destroy_lane(pluq_ctx* l) {
   if (!l) return;
   destroy_lane(l->lane[0]);
   destroy_lane(l->lane[1]);
+  destroy_lane(l->lane[2]);
+  for (cudaEvent_t e : l->la_ev)
+    if (e) cudaEventDestroy(e);
   l->perm_r = DevBuf{};  // views of the parent's buffers
   l->perm_c = DevBuf{};
   l->inv_table = DevBuf{};
@@ -335,6 +338,7 @@ int get_lane(pluq_ctx* c, int i, int64_t m, int64_t n, pluq_ctx** out) {
   l->limb_plan_p = c->limb_plan_p;
   for (int k = 0; k < 6; ++k) l->limb_plan[k] = c->limb_plan[k];
   l->limb_variant = c->limb_variant;
+  l->lookahead = c->lookahead;
   l->fused_kmax = c->fused_kmax;
   l->perm_r = c->perm_r;
   l->perm_c = c->perm_c;
@@ -472,8 +476,14 @@ struct Recursion {
 
   // The updates after A1 on two streams (see node); returns once this
   // context's stream waits for the other's work (no host synchronisation).
+  // With h1 > 0 (F and G empty: r1 = m1 = n1), H's update is split at R's
+  // first quarter: H11 (h1 x w1) on this stream, the rest on the look-ahead
+  // child context's stream, whose completion *la_done then records; R's
+  // recursion starts on H11 at once and waits for la_done only after its own
+  // A1 (see node).
   int side_stream_update(int64_t R0, int64_t C0, int64_t m1, int64_t n1, int64_t m2, int64_t n2,
-                         int64_t r1) {
+                         int64_t r1, int d = 0, int64_t h1 = 0, int64_t w1 = 0,
+                         cudaEvent_t* la_done = nullptr) {
     const int64_t m = m1 + m2;
     pluq_ctx* lg = nullptr;
     PLUQ_TRY(get_lane(c, 1, m2, n1, &lg));
@@ -491,8 +501,33 @@ struct Recursion {
     // this stream: D, then [F; H] -= [M1; E] D once E is ready
     PLUQ_TRY(trsm_left_lower_unit(c, X(R0, C0, 0, 0), lda, r1, X(R0, C0, 0, n1), lda, n2, diag0));
     PLUQ_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[0], 0));
-    PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
-                       X(R0, C0, r1, n1), lda));
+    if (h1 > 0) {
+      pluq_ctx* la = nullptr;
+      PLUQ_TRY(get_lane(c, 2, m2, n2, &la));
+      if ((int)c->la_ev.size() < 2 * (d + 1)) c->la_ev.resize(2 * (d + 1), nullptr);
+      for (int k = 0; k < 2; ++k)
+        if (!c->la_ev[2 * d + k])
+          PLUQ_CUDA(cudaEventCreateWithFlags(&c->la_ev[2 * d + k], cudaEventDisableTiming));
+      PLUQ_CUDA(cudaEventRecord(c->la_ev[2 * d], c->stream));  // D and E ready
+      PLUQ_CUDA(cudaStreamWaitEvent(la->stream, c->la_ev[2 * d], 0));
+      PLUQ_TRY(fgemm_sub(c, h1, w1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, n1), lda,
+                         X(R0, C0, m1, n1), lda));
+      PLUQ_TRY(fgemm_sub(la, h1, n2 - w1, r1, X(R0, C0, m1, 0), lda, X(R0, C0, 0, n1 + w1), lda,
+                         X(R0, C0, m1, n1 + w1), lda));
+      PLUQ_TRY(fgemm_sub(la, m2 - h1, n2, r1, X(R0, C0, m1 + h1, 0), lda, X(R0, C0, 0, n1), lda,
+                         X(R0, C0, m1 + h1, n1), lda));
+      // its device error word joins this context's before the hand-over
+      k_merge_err<<<1, 1, 0, la->stream>>>(c->small.as<int>() + 16, la->small.as<int>() + 16);
+      PLUQ_CUDA(cudaGetLastError());
+      PLUQ_CUDA(cudaEventRecord(c->la_ev[2 * d + 1], la->stream));
+      *la_done = c->la_ev[2 * d + 1];
+      merge_lane_stats(c, la);
+      for (int k = 0; k < PC_COUNT; ++k) la->launches[k] = 0;
+      la->n_base = la->n_nodes = la->n_gemm = 0;
+    } else {
+      PLUQ_TRY(fgemm_sub(c, m - r1, n2, r1, X(R0, C0, r1, 0), lda, X(R0, C0, 0, n1), lda,
+                         X(R0, C0, r1, n1), lda));
+    }
     PLUQ_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[1], 0));
     // the other stream's device error word joins this context's
     k_merge_err<<<1, 1, 0, c->stream>>>(c->small.as<int>() + 16, lg->small.as<int>() + 16);
@@ -516,8 +551,10 @@ struct Recursion {
   // Factors the m x n block at (R0, C0); *r_out receives its rank and *id
   // whether its local row / column index vectors are the identity (then the
   // caller's permutations of the blocks beside it are no-ops and skipped).
+  // pending: an event the blocks beside A1 (A2, A3, A4) wait for before this
+  // node touches them (the look-ahead update of the parent's H), or null.
   int node(int64_t R0, int64_t C0, int64_t m, int64_t n, int d, int64_t* r_out, Ident* id,
-           int keep = KEEP_LU) {
+           int keep = KEEP_LU, cudaEvent_t pending = nullptr) {
     int32_t* pr = PR(d) + R0;
     int32_t* pc = PC(d) + C0;
     *r_out = 0;
@@ -605,6 +642,7 @@ struct Recursion {
       }
     }
     const int64_t m2 = m - m1, n2 = n - n1;
+    cudaEvent_t la_pending = nullptr;  // this node's look-ahead update of R's A2, A3, A4
     int32_t* cr = PR(d + 1);
     int32_t* cc = PC(d + 1);
     PLUQ_TRY(launch_iota_pair(c, pr, m, pc, n));
@@ -613,6 +651,8 @@ struct Recursion {
     int64_t r1 = 0;
     Ident id1, id2, id3, id4;
     PLUQ_TRY(node(R0, C0, m1, n1, d + 1, &r1, &id1, KEEP_LU));
+    // the parent's look-ahead update of this block's A2, A3, A4
+    if (pending) PLUQ_CUDA(cudaStreamWaitEvent(c->stream, pending, 0));
     if (r1 < m1 || r1 < n1) {
       // F or G is non-empty: blocks move by shifts, the diagonal blocks of later
       // triangles are no longer the cached leaves
@@ -627,7 +667,13 @@ struct Recursion {
       // stream while this one solves D, then [F; H] -= [M1; E] D waits for E
       const bool side = c->lane_depth < c->fork_depth && !c->prof.on && m2 > 0 &&
                         (int64_t)r1 * (m2 + n2) >= kForkMinElems * 64;
-      if (side) {
+      // look-ahead: A1 of full rank (F and G empty) and an R that splits
+      const bool la = side && c->lookahead && c->decomposition == 0 && r1 == m1 && r1 == n1 &&
+                      m2 > lim_m && n2 > lim_n;
+      if (la) {
+        PLUQ_TRY(side_stream_update(R0, C0, m1, n1, m2, n2, r1, d, split(m2), split(n2),
+                                    &la_pending));
+      } else if (side) {
         PLUQ_TRY(side_stream_update(R0, C0, m1, n1, m2, n2, r1));
       } else {
         const int64_t diag0 = R0 == C0 ? R0 : -1;
@@ -680,7 +726,8 @@ struct Recursion {
 
     // R
     int64_t r4 = 0;
-    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4, &id4, keep));
+    PLUQ_TRY(node(R0 + m1 + r3, C0 + n1 + r2, m2 - r3, n2 - r2, d + 1, &r4, &id4, keep,
+                  la_pending));
     PLUQ_TRY(compose_pair(pr + m1 + r3, cr + R0 + m1 + r3, m2 - r3, pc + n1 + r2,
                           cc + C0 + n1 + r2, n2 - r2, id4));
     // E2, M3 (columns 0..r1+r3) and K (columns n1..n1+r2) by R's row
@@ -947,6 +994,9 @@ int pluq_destroy(pluq_ctx* c) {
   cudaDeviceSynchronize();
   destroy_lane(c->lane[0]);
   destroy_lane(c->lane[1]);
+  destroy_lane(c->lane[2]);
+  for (cudaEvent_t e : c->la_ev)
+    if (e) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   for (cudaEvent_t e : c->side_ev)
     if (e) cudaEventDestroy(e);
@@ -1402,6 +1452,10 @@ int pluq_set_option(pluq_ctx* c, int option, int value) {
     case PLUQ_OPT_WINOGRAD_MIN:
       if (value < 0) return PLUQ_ERR_INVALID_ARG;
       c->wino_min = value;
+      return PLUQ_OK;
+    case PLUQ_OPT_LOOKAHEAD:
+      if (value < 0 || value > 1) return PLUQ_ERR_INVALID_ARG;
+      c->lookahead = value;
       return PLUQ_OK;
     case PLUQ_OPT_BATCH_SLAB:
       if (value != 0 && value != 16 && value != 24 && value != 32) return PLUQ_ERR_INVALID_ARG;

@@ -547,6 +547,31 @@ def test_pluq_cached_diagonal_inverses(ctx, form, fork_depth, leaf, p, shape, ki
         ctx.set_option("fork_depth", 2)
 
 
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("fork_depth", [1, 2])
+@pytest.mark.parametrize("p,shape,kind", [(65521, (1536, 1536), "uniform"),
+                                          (131071, (1300, 1700), "uniform"),
+                                          (3, (1100, 1000), "uniform"),
+                                          (65521, (1536, 1536), "lru")])
+def test_pluq_lookahead(ctx, form, fork_depth, p, shape, kind):
+    """The look-ahead split of H's update (H11 on the main stream, the rest on a
+    third stream while R's recursion factors H11) gives the oracle's result, with
+    it on and off, on full-rank leading blocks (where it applies), ragged shapes
+    and rank-deficient ones (where it does not)."""
+    m, n = shape
+    A = (workloads.uniform_matrix(m, n, p, 23) if kind == "uniform"
+         else workloads.prescribed_rank_matrix(m, n, m // 2, p, 23).A)
+    ctx.set_option("fork_depth", fork_depth)
+    try:
+        for on in (1, 0):
+            ctx.set_option("lookahead", on)
+            with leaf_mode(ctx, (128, 1)):
+                assert_parity(ctx, A, p, form)
+    finally:
+        ctx.set_option("lookahead", 0)
+        ctx.set_option("fork_depth", 2)
+
+
 @pytest.mark.parametrize("tb", [1, 7, 16, 64])
 def test_pluq_trsm_blocks(ctx, tb):
     p = 65521
