@@ -173,9 +173,12 @@ int fgemm_modp_noalloc(uint32_t p, int64_t M, int64_t N, int64_t K, const uint32
  * the batching of many small rank-deficient factorizations in one persistent,
  * graph-captured launch.  Matrices with m, n <= 1024 are taken by CTAs of one
  * persistent kernel from a work counter (largest first), one CTA per matrix,
- * each running the rank-profile-revealing elimination of Sec. 4.1; the
- * launch and its descriptor / result copies are captured once in a CUDA graph
- * per batch size and replayed.  Larger matrices are factored one by one.
+ * each running the rank-profile-revealing elimination of Sec. 4.1 (rows in
+ * order) blocked by slabs of pivots collected in shared memory, the rows below
+ * each slab updated at once (tensor cores for p < 2^16).  The launch and its
+ * descriptor / result copies are captured once in a CUDA graph per batch size
+ * and replayed.  Larger matrices are factored one by one (`form` selects their
+ * product form).
  *   m, n, lda   host int64 arrays of length batch.
  *   A, P, Q     host arrays of `batch` device pointers.
  *   ranks       host int64 array of length batch; receives the ranks.
