@@ -793,11 +793,13 @@ def test_batched_parity(ctx, p):
             check_pluq(A, p, P, Q, Ad.cpu().numpy().astype(np.int64), r)
 
 
+@pytest.mark.parametrize("p", [2, 65521, 131071, 2147483647])
 @pytest.mark.parametrize("slab", [16, 24, 32])
-def test_batched_slab_heights(slab):
+def test_batched_slab_heights(slab, p):
     """Each buffer height of the batched kernel (pivots a slab collects before
-    updating the rows below) against the oracle on the mixed batch."""
-    p = 65521
+    updating the rows below) against the oracle on the mixed batch, in every
+    field mode (bits, 16-bit buffer and tensor-core updates, one reduction per
+    dot product, a reduction per product)."""
     c = pq.Context(0)
     try:
         c.set_option("batch_slab", slab)
