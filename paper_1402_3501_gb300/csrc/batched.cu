@@ -26,11 +26,13 @@
 //      pivot rows move up.
 // The slab closes once fewer than kSlab / 4 buffer rows are free (or the matrix
 // ends): its pivot rows go back to the matrix and the rows below are reduced by
-// its pivots at once, L from a forward substitution per row, then C <- C - L U
-// in 64 x 64 tiles of 4 x 4 register micro-tiles.  Multipliers are kept in
-// Montgomery form (x R mod p, R = 2^32) as left operands, so the reduction of
-// a sum of products (L R) * U is one REDC.  L multipliers overwrite the pivot
-// column entries.
+// its pivots at once.  For p < 2^16 on the tensor cores (trailing_mma, with
+// W = U_JJ^{-1} U formed once a slab, so the multipliers come out of the same
+// products); otherwise L from a forward substitution per row, then C <- C - L U
+// in 64 x 64 tiles of 4 x 4 register micro-tiles on the CUDA cores.  One factor
+// of every product is kept in Montgomery form (x R mod p, R = 2^32), so the
+// reduction of a sum of products is one REDC.  L multipliers overwrite the
+// pivot column entries.  For p < 2^16 the buffer holds 16-bit residues.
 //
 // The final P^T A Q^T layout is written in place: the multipliers of the
 // non-pivot rows are first copied to the CTA's scratch, the pivot rows are then
@@ -253,10 +255,10 @@ __host__ __device__ constexpr size_t slab_smem_bytes_for(int ldN) {
                        + (size_t)kSlab * kLdE)        // Uinv: U_JJ^{-1} of the tensor-core update
          + 4 * ((size_t)kSlab * kLdL                  // LT: multipliers (or entries) of a row block
                 + (size_t)kSlab * kSlab               // Ls: multipliers of the buffer rows (plain)
-                + 6 * kSlab                      // spr, spc, invm, first, srow, pslot
-                + (size_t)ldN                    // ispiv
-                + (size_t)kBatchMax              // prow, pcol (16-bit)
-                + kBatchWarps + 8);              // red, misc
+                + 6 * kSlab                           // spr, spc, invm, first, srow, pslot
+                + (size_t)ldN                         // ispiv
+                + (size_t)kBatchMax                   // prow, pcol (16-bit)
+                + kBatchWarps + 8);                   // red, misc
 }
 
 
