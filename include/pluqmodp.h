@@ -230,6 +230,16 @@ int echelon_modp_batched(pluq_ctx* ctx, uint32_t p, int32_t batch, const int64_t
 /* Host copy of the rank found by the last factorization on this context. */
 int pluq_last_rank(pluq_ctx* ctx, int64_t* rank);
 
+/* Waits for the work the context has issued on its stream (the stream of its
+ * last call) and returns the device-side status of that work: the context's
+ * device error word (PLUQ_ERR_TIMEOUT when a bounded device wait ran out), else
+ * PLUQ_ERR_CUDA for an asynchronous CUDA error, else PLUQ_OK.  The entry points
+ * above already return once their results are complete (the recursion reads
+ * each leaf's rank on the host), so this is the check for callers that queue
+ * their own work on the same stream after a call.  The error word is cleared by
+ * the context's next call. */
+int pluq_sync_status(pluq_ctx* ctx);
+
 /* Tuning knobs of the recursion (base-case tile bm x bn, 1..128 each, and the
  * diagonal block of the triangular solves, 1..64).  0 keeps the current
  * value. */

@@ -10,7 +10,7 @@ from .binding import (BatchPlan, FORM_AUTO, FORM_FP64, FORM_LIMB_F16, Context, P
                       column_echelon_modp, default_context, echelon_modp, echelon_modp_batched,
                       fgemm_modp,
                       fgemm_modp_noalloc, load, pluq_modp, pluq_modp_batched, rank_profile_modp,
-                      rank_profile_modp_batched)
+                      rank_profile_modp_batched, sync_status)
 
 __all__ = [
     "BatchPlan",
@@ -18,4 +18,5 @@ __all__ = [
     "column_echelon_modp", "default_context", "echelon_modp", "echelon_modp_batched", "fgemm_modp",
     "fgemm_modp_noalloc",
     "load", "pluq_modp", "pluq_modp_batched", "rank_profile_modp", "rank_profile_modp_batched",
+    "sync_status",
 ]

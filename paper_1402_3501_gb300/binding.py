@@ -36,7 +36,7 @@ SYMBOLS = [
     "fgemm_modp", "pluq_modp_batched", "pluq_last_rank", "pluq_set_tuning", "pluq_last_stats",
     "pluq_status_string", "pluq_profile_enable", "pluq_profile_read", "pluq_set_leaf",
     "fgemm_modp_noalloc", "pluq_set_option", "pluq_autotune", "column_echelon_modp",
-    "rank_profile_modp_batched", "echelon_modp_batched",
+    "rank_profile_modp_batched", "echelon_modp_batched", "pluq_sync_status",
 ]
 
 
@@ -68,6 +68,7 @@ def load():
         "rank_profile_modp_batched": [vp, u32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32,
                                       vp],
         "pluq_last_rank": [vp, vp],
+        "pluq_sync_status": [vp],
         "pluq_set_tuning": [vp, i32, i32, i32],
         "pluq_last_stats": [vp, vp, vp, vp],
         "pluq_status_string": [i32],
@@ -479,6 +480,11 @@ def rank_profile_modp_batched(As: list, p: int, form="auto", ctx: Context | None
         return outs + (list(status),)
     _check(st, "rank_profile_modp_batched")
     return outs
+
+
+def sync_status(ctx: Context) -> int:
+    """Waits for the context's stream; the status of its device work (0: OK)."""
+    return int(load().pluq_sync_status(ctx.handle))
 
 
 def last_rank(ctx: Context) -> int:

@@ -1372,6 +1372,19 @@ int pluq_last_rank(pluq_ctx* c, int64_t* rank) {
   return PLUQ_OK;
 }
 
+int pluq_sync_status(pluq_ctx* c) {
+  if (!c) return PLUQ_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaGetLastError() != cudaSuccess)
+    return PLUQ_ERR_CUDA;
+  if (!c->small.ptr) return PLUQ_OK;
+  int32_t word = 0;
+  if (cudaMemcpy(&word, c->small.as<int32_t>() + 16, sizeof(word), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return PLUQ_ERR_CUDA;
+  return word != 0 ? word : PLUQ_OK;
+}
+
 int pluq_set_tuning(pluq_ctx* c, int bm, int bn, int trsm_block) {
   if (!c) return PLUQ_ERR_INVALID_ARG;
   if (bm < 0 || bm > 128 || bn < 0 || bn > 128 || trsm_block < 0 || trsm_block > 64)

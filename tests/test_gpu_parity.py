@@ -714,8 +714,10 @@ def test_wait_limit_runs_out(kind):
         with pytest.raises(pq.PluqError) as e:
             pq.pluq_modp(to_dev(A), p, ctx=c)
         assert e.value.status == -8  # PLUQ_ERR_TIMEOUT
+        assert pq.sync_status(c) == -8  # the device error word until the next call
         c.set_option("wait_limit_us", 2000000)
         assert_parity(c, A, p)
+        assert pq.sync_status(c) == 0
     finally:
         c.close()
 
