@@ -309,6 +309,8 @@ int trsm_right_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uin
                      int64_t ldb, int64_t nrows, int64_t diag0 = -1);
 // -L^{-1}, -U^{-1} of the full-rank dinv_b x dinv_b block T into cache slot `slot`
 int cache_leaf_inverses(pluq_ctx* c, const uint32_t* T, int64_t ldt, int64_t slot);
+int cache_leaf_inverse(pluq_ctx* w, pluq_ctx* c, bool upper, const uint32_t* T, int64_t ldt,
+                       int64_t slot);
 int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
                     int64_t ldb, int64_t ncols);
 // one-launch solves of a triangle of at most strip_rows(c, count) rows (its

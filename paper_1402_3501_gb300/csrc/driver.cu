@@ -607,7 +607,26 @@ struct Recursion {
       const int64_t b = c->dinv_b;
       if (b > 0 && c->dinv_ok && m == b && n == b && *r_out == b && R0 == C0 && R0 % b == 0 &&
           R0 / b < (int64_t)c->dinv_valid.size()) {
-        PLUQ_TRY(cache_leaf_inverses(c, X(R0, C0, 0, 0), lda, R0 / b));
+        if (!c->prof.on && c->lane_depth < c->fork_depth) {
+          // the two triangles at once: U's on the G child context's stream
+          pluq_ctx* lg = nullptr;
+          PLUQ_TRY(get_lane(c, 1, b, b, &lg));
+          for (cudaEvent_t* e : {&c->fork_ev, &c->side_ev[0]})
+            if (!*e) PLUQ_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+          PLUQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+          PLUQ_CUDA(cudaStreamWaitEvent(lg->stream, c->fork_ev, 0));
+          PLUQ_TRY(cache_leaf_inverse(lg, c, true, X(R0, C0, 0, 0), lda, R0 / b));
+          k_merge_err<<<1, 1, 0, lg->stream>>>(c->small.as<int>() + 16, lg->small.as<int>() + 16);
+          PLUQ_CUDA(cudaGetLastError());
+          PLUQ_CUDA(cudaEventRecord(c->side_ev[0], lg->stream));
+          PLUQ_TRY(cache_leaf_inverse(c, c, false, X(R0, C0, 0, 0), lda, R0 / b));
+          PLUQ_CUDA(cudaStreamWaitEvent(c->stream, c->side_ev[0], 0));
+          merge_lane_stats(c, lg);
+          for (int k = 0; k < PC_COUNT; ++k) lg->launches[k] = 0;
+          lg->n_base = lg->n_nodes = lg->n_gemm = 0;
+        } else {
+          PLUQ_TRY(cache_leaf_inverses(c, X(R0, C0, 0, 0), lda, R0 / b));
+        }
         c->dinv_valid[R0 / b] = 1;
       }
       return PLUQ_OK;

@@ -423,24 +423,33 @@ __global__ void k_negate(uint32_t* __restrict__ X, int64_t count, uint32_t p) {
     X[t] = X[t] == 0u ? 0u : p - X[t];
 }
 
-int cache_leaf_inverses(pluq_ctx* c, const uint32_t* T, int64_t ldt, int64_t slot) {
+// One of the two: -(L^{-1}) (upper = false) or -(U^{-1}) into c's slot, the work
+// issued on w's stream with w's workspace (w = c, or a child context of c so
+// that the two triangles are inverted at once).
+int cache_leaf_inverse(pluq_ctx* w, pluq_ctx* c, bool upper, const uint32_t* T, int64_t ldt,
+                       int64_t slot) {
   const int64_t b = c->dinv_b;
-  uint32_t* Li = c->dinv.as<uint32_t>() + (slot * 2) * b * b;
-  uint32_t* Ui = Li + b * b;
+  uint32_t* X = c->dinv.as<uint32_t>() + (slot * 2 + (upper ? 1 : 0)) * b * b;
   {
-    ProfScope ps(c, PC_TRSM, 0, 8.0 * b * b, 2);
-    k_identity<<<block_grid(b, b), 256, 0, c->stream>>>(Li, b);
-    k_identity<<<block_grid(b, b), 256, 0, c->stream>>>(Ui, b);
+    ProfScope ps(w, PC_TRSM, 0, 4.0 * b * b);
+    k_identity<<<block_grid(b, b), 256, 0, w->stream>>>(X, b);
     PLUQ_CUDA(cudaGetLastError());
   }
-  PLUQ_TRY(trsm_left_lower_unit(c, T, ldt, b, Li, b, b, -1));
-  PLUQ_TRY(trsm_right_upper(c, T, ldt, b, Ui, b, b, -1));
+  if (upper)
+    PLUQ_TRY(trsm_right_upper(w, T, ldt, b, X, b, b, -1));
+  else
+    PLUQ_TRY(trsm_left_lower_unit(w, T, ldt, b, X, b, b, -1));
   {
-    ProfScope ps(c, PC_TRSM, 0, 16.0 * b * b);
-    k_negate<<<(unsigned)cdiv(2 * b * b, 256 * 8), 256, 0, c->stream>>>(Li, 2 * b * b, c->F.p);
+    ProfScope ps(w, PC_TRSM, 0, 8.0 * b * b);
+    k_negate<<<(unsigned)cdiv(b * b, 256 * 8), 256, 0, w->stream>>>(X, b * b, c->F.p);
     PLUQ_CUDA(cudaGetLastError());
   }
   return PLUQ_OK;
+}
+
+int cache_leaf_inverses(pluq_ctx* c, const uint32_t* T, int64_t ldt, int64_t slot) {
+  PLUQ_TRY(cache_leaf_inverse(c, c, false, T, ldt, slot));
+  return cache_leaf_inverse(c, c, true, T, ldt, slot);
 }
 
 int trsm_left_upper(pluq_ctx* c, const uint32_t* U, int64_t ldu, int64_t r, uint32_t* B,
